@@ -1,0 +1,546 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the ttv / ttm / entrywise hot path on GB300.
+
+One step is one pass of the whole hot path over the order-4 FP32 workload
+128x128x128x128 (1 GiB, N(0,1)) held in both the first-order and the
+last-order layout: ttv along each mode q = 1..4 with a length-128 vector,
+ttm along each mode with a 128x128 matrix (FP32-accurate: split-BF16x3 on the
+tensor cores where the library selects them, else FP32 SIMT), for both
+layouts, plus the layout-mixed entrywise add of the two copies: 17 calls.
+
+`value` is algorithmic bytes moved per second (GB/s) over the whole job with
+the inputs resident in HBM; `e2e` is the same metric through the C ABI with
+the inputs copied in from pinned host memory and every output copied back
+inside the timed region.  Inputs (1 GiB each) are larger than L2, so no L2
+flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tlgb|reference]
+
+`--impl reference` times the FP64 CPU oracle (the plain definition of each
+operation) on a bounded sample of the same workload on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ttv/ttm GB/s & TFLOP/s vs roofline; served ops/s and p99 latency vs plain"
+WORKLOAD = "order-4 FP32 128^4 (1 GiB), first- and last-order layouts: ttv q=1..4, ttm q=1..4 " \
+           "(128x128), entrywise add of the two layouts"
+SM_COUNT = 152
+FP32_ALU_TFLOPS = SM_COUNT * 128 * 2 * 2.07e9 / 1e12    # 128 FP32 lanes/SM at 2070 MHz
+FP64_ALU_TFLOPS = 1.25                                   # nominal GB300 FP64 rate
+TTM_PRECISION_NAME = {0: "f32", 2: "f32", 3: "tf32", 4: "bf16", 5: "bf16x3"}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tlgb", choices=["tlgb", "reference"])
+    ap.add_argument("--edge", type=int, default=128, help="extent of every mode (workload size)")
+    ap.add_argument("--ttm-precision", type=int, default=2,
+                    help="TL_P_* for the ttm calls (2 = FP32 SIMT, 5 = split-BF16x3)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 19,
+                    help="outputs per ttv/ttm op in the CPU-oracle sample")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- setup ---
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks / throttle reasons every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(mhz), "reasons": sorted(reasons)}
+
+
+def gpu_id(torch, dev):
+    """nvidia-smi identifier of the device (its UUID, else the ordinal)."""
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev.index or 0)
+
+
+def src_sha(path):
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when absent or when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    e = d.get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_1711_10912_gb300", "csrc", e["source"])
+    if not os.path.exists(src) or src_sha(src) != e.get("source_sha256"):
+        return None
+    return e["dram_bytes_per_launch"]
+
+
+# -------------------------------------------------------------- workload ---
+
+class Workload:
+    """Device buffers, descriptors and the 17 calls of one step."""
+
+    def __init__(self, tl, torch, dev, edge, ttm_precision, seed_case):
+        import synth
+        self.tl, self.torch, self.dev = tl, torch, dev
+        p = 4
+        n = (edge,) * p
+        self.n = n
+        self.N = edge ** p
+        case = seed_case
+        self.memF = case.mem_first
+        X = synth.from_memory(self.memF, n, synth.first_order(p))
+        self.memL = synth.to_memory(X, synth.last_order(p))
+        del X
+        f32 = torch.float32
+        self.AF = torch.from_numpy(self.memF).to(dev)
+        self.AL = torch.from_numpy(self.memL).to(dev)
+        self.b = [torch.from_numpy(v).to(dev) for v in case.vectors]
+        self.B = [torch.from_numpy(np.ascontiguousarray(m).reshape(-1)).to(dev)
+                  for m in case.matrices]
+        self.Cv = torch.empty(self.N // edge, dtype=f32, device=dev)
+        self.Cm = torch.empty(self.N, dtype=f32, device=dev)
+        self.Ce = torch.empty(self.N, dtype=f32, device=dev)
+        self.ttm_precision = ttm_precision
+        self.layouts = [("first", synth.first_order(p), self.AF), ("last", synth.last_order(p), self.AL)]
+        self.calls = []
+        for lname, pi, Ad in self.layouts:
+            DA = tl.Desc(Ad, n, pi)
+            for q in range(1, p + 1):
+                nout = tuple(x for r, x in enumerate(n) if r != q - 1)
+                pic = tuple(sorted(r for r in pi if r != q).index(r) + 1 for r in pi if r != q)
+                self.calls.append(("ttv", lname, q, DA, tl.Desc(self.Cv, nout, pic)))
+            for q in range(1, p + 1):
+                self.calls.append(("ttm", lname, q, DA, tl.Desc(self.Cm, n, pi)))
+        self.calls.append(("entrywise", "first+last", 0, tl.Desc(self.AF, n, synth.first_order(p)),
+                           tl.Desc(self.AL, n, synth.last_order(p)), tl.Desc(self.Ce, n)))
+        # algorithmic bytes / flops per call
+        e = 4
+        self.bytes = {"ttv": (self.N + self.N // edge + edge) * e,
+                      "ttm": (2 * self.N + edge * edge) * e,
+                      "entrywise": 3 * self.N * e}
+        self.flops = {"ttv": 2 * self.N, "ttm": 2 * self.N * edge, "entrywise": self.N}
+        self.step_bytes = sum(self.bytes[c[0]] for c in self.calls)
+        self.step_flops = sum(self.flops[c[0]] for c in self.calls)
+
+    def run_call(self, c, stream_handle):
+        tl = self.tl
+        kind = c[0]
+        if kind == "ttv":
+            q = c[2]
+            rc = tl.tl_ttv(c[3], self.b[q - 1], 1, q, c[4], 0, stream_handle)
+        elif kind == "ttm":
+            q = c[2]
+            edge = self.n[0]
+            rc = tl.tl_ttm(c[3], self.B[q - 1], edge, edge, 1, q, c[4], self.ttm_precision, 0,
+                           stream_handle)
+        else:
+            rc = tl.tl_entrywise(tl.TL_ADD, c[3], c[4], 1.0, c[5], stream_handle)
+        tl.check(rc, kind)
+
+    def run_step(self, stream_handle, events=None):
+        for i, c in enumerate(self.calls):
+            if events is not None:
+                events[i][0].record()
+            self.run_call(c, stream_handle)
+            if events is not None:
+                events[i][1].record()
+
+
+def kernel_of(tl, wl, c):
+    """Kernel name the library plans for call c (host-side plan)."""
+    if c[0] == "ttv":
+        rc, js = tl.tl_plan_describe(tl.TL_OP_TTV, c[3], None, c[2], 0, 0, 0, c[4])
+    elif c[0] == "ttm":
+        rc, js = tl.tl_plan_describe(tl.TL_OP_TTM, c[3], None, c[2], wl.n[0], wl.ttm_precision, 0,
+                                     c[4])
+    else:
+        rc, js = tl.tl_plan_describe(tl.TL_OP_ENTRYWISE, c[3], c[4], 0, 0, 0, tl.TL_ADD, c[5])
+    return json.loads(js)["kernel"] if rc == 0 else "?"
+
+
+# ------------------------------------------------------------ CPU oracle ---
+
+def cpu_oracle_sample(case, memF64, memL64, edge, per_op, g):
+    """Times the FP64 oracle on a bounded sample of one step: per_op sampled
+    outputs of every ttv and ttm call and a per_op*edge-element block of the
+    entrywise add.  Returns (seconds, algorithmic bytes represented)."""
+    import oracle
+    import synth
+    p = 4
+    n = (edge,) * p
+    N = edge ** p
+    sec, byts = 0.0, 0.0
+    b_ttv = (N + N // edge + edge) * 4
+    b_ttm = (2 * N + edge * edge) * 4
+    for pi, mem in ((synth.first_order(p), memF64), (synth.last_order(p), memL64)):
+        w = oracle.strides(n, pi)
+        for q in range(1, p + 1):
+            idx = np.stack([g.integers(0, edge, size=per_op) for _ in range(p - 1)], axis=1)
+            bq = case.vectors[q - 1].astype(np.float64)
+            t0 = time.perf_counter()
+            oracle.ttv_at(mem, n, w, q, bq, idx)
+            sec += time.perf_counter() - t0
+            byts += b_ttv * per_op / (N // edge)
+        for q in range(1, p + 1):
+            idx = np.stack([g.integers(0, edge, size=per_op) for _ in range(p)], axis=1)
+            Bq = case.matrices[q - 1].astype(np.float64).reshape(-1)
+            t0 = time.perf_counter()
+            oracle.ttm_at(mem, n, w, q, Bq, edge, 1, idx)
+            sec += time.perf_counter() - t0
+            byts += b_ttm * per_op / N
+    # entrywise add over the first `s` slices of mode 4 of both layouts
+    s = max(1, min(edge, per_op * edge // (edge ** 3)))
+    nsub = (edge, edge, edge, s)
+    wF = oracle.strides(n, synth.first_order(p))
+    wL = oracle.strides(n, synth.last_order(p))
+    t0 = time.perf_counter()
+    oracle.entrywise(oracle.OP_ADD, nsub, memF64, wF, memL64, wL)
+    sec += time.perf_counter() - t0
+    byts += 3 * 4 * edge ** 3 * s
+    return sec, byts
+
+
+def cpu_baseline(case, edge, per_op):
+    import synth
+    memF64 = case.mem_first.astype(np.float64)
+    X = synth.from_memory(case.mem_first, (edge,) * 4, synth.first_order(4))
+    memL64 = synth.to_memory(X, synth.last_order(4)).astype(np.float64)
+    del X
+    g = synth.rng(99)
+    sec, byts = cpu_oracle_sample(case, memF64, memL64, edge, per_op, g)
+    return {"value": byts / sec / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "seconds": round(sec, 3),
+            "sample": f"{per_op} sampled outputs of each of the 8 ttv and 8 ttm calls, and a "
+                      f"{edge}^3 x {max(1, min(edge, per_op * edge // edge ** 3))} block of the "
+                      "entrywise add, FP64 oracle single-threaded; bytes scaled by the sampled "
+                      "fraction of each call"}
+
+
+# ------------------------------------------------------------ main arms ---
+
+def reference_arm(args):
+    """The FP64 CPU oracle as the reference implementation, on a bounded
+    sample of the workload per step (rank 0 only)."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    edge = args.edge
+    case = synth.scale_case(edge=edge)
+    memF64 = case.mem_first.astype(np.float64)
+    X = synth.from_memory(case.mem_first, (edge,) * 4, synth.first_order(4))
+    memL64 = synth.to_memory(X, synth.last_order(4)).astype(np.float64)
+    del X
+    per_op = 1 << 15
+    g = synth.rng(7)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(case, memF64, memL64, edge, per_op, g)
+    tot_s, tot_b = 0.0, 0.0
+    for _ in range(args.steps):
+        s, b = cpu_oracle_sample(case, memF64, memL64, edge, per_op, g)
+        tot_s += s
+        tot_b += b
+    v = tot_b / tot_s / 1e9
+    line = {"metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot_s / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "edge": edge, "l2": "inputs larger than L2",
+                       "parallelism": "single process, host CPU"},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_op} sampled outputs per ttv/ttm call and a "
+                                       "slice block of the add per step"},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import synth
+    from paper_1711_10912_gb300 import build as tlbuild
+    import paper_1711_10912_gb300 as tl
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        tlbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    tl.load_library()
+
+    peaks, peak_src = load_peaks()
+    edge = args.edge
+    case = synth.scale_case(edge=edge)
+    wl = Workload(tl, torch, dev, edge, args.ttm_precision, case)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up (also plans and allocates any workspace)
+    for _ in range(max(args.warmup, 0)):
+        wl.run_step(sh)
+    torch.cuda.synchronize()
+
+    # ------------------------------------------- device-resident timed run
+    ncalls = len(wl.calls)
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+            for _ in range(ncalls)] for _ in range(args.steps)]
+    sampler = ClockSampler(gpu_id(torch, dev))
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = tl.tl_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record()
+    for k in range(args.steps):
+        wl.run_step(sh, evs[k])
+    t_end.record()
+    torch.cuda.synchronize()
+    barrier()
+    launches = tl.tl_launch_count() - launches0
+    clocks = sampler.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = wl.step_bytes * world * args.steps / (elapsed_ms / 1e3) / 1e9
+
+    # per-call durations and the dominant kernel
+    per_call = [[evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(args.steps)]
+                for i in range(ncalls)]
+    kern = [kernel_of(tl, wl, c) for c in wl.calls]
+    by_kernel = {}
+    for i, c in enumerate(wl.calls):
+        d = by_kernel.setdefault(kern[i], {"ms": 0.0, "launches": 0, "bytes": 0, "flops": 0,
+                                           "op": c[0]})
+        d["ms"] += sum(per_call[i])
+        d["launches"] += args.steps
+        d["bytes"] += wl.bytes[c[0]] * args.steps
+        d["flops"] += wl.flops[c[0]] * args.steps
+    tot_ms = sum(d["ms"] for d in by_kernel.values())
+    breakdown = {}
+    for kname, d in by_kernel.items():
+        avg = d["ms"] / d["launches"]
+        breakdown[kname] = {"op": d["op"], "launches": d["launches"], "avg_ms": round(avg, 4),
+                            "share": round(d["ms"] / tot_ms, 4),
+                            "GB/s": round(d["bytes"] / (d["ms"] / 1e3) / 1e9, 1),
+                            "TFLOP/s": round(d["flops"] / (d["ms"] / 1e3) / 1e12, 2)}
+    per_op_q = {}
+    for i, c in enumerate(wl.calls):
+        key = f"{c[0]}_{c[1]}_q{c[2]}" if c[0] != "entrywise" else "add_first+last"
+        med = statistics.median(per_call[i])
+        per_op_q[key] = {"kernel": kern[i], "ms": round(med, 4),
+                         "GB/s": round(wl.bytes[c[0]] / (med / 1e3) / 1e9, 1)}
+    dom = max(by_kernel, key=lambda k: by_kernel[k]["ms"])
+    d = by_kernel[dom]
+    avg_s = d["ms"] / d["launches"] / 1e3
+    per_launch_bytes = d["bytes"] / d["launches"]
+    per_launch_flops = d["flops"] / d["launches"]
+    if dom == "ttm_simt":
+        roof = {"bound": "alu", "achieved": per_launch_flops / avg_s / 1e12,
+                "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": per_launch_bytes / avg_s / 1e9,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "peak_source": f"{peak_src} hbm_gbs"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["traffic"] = traffic_for(dom)
+    roof["algorithmic_per_launch"] = per_launch_bytes if roof["unit"] == "GB/s" else per_launch_flops
+
+    # ------------------------------------------------------- end to end
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(tl, torch, wl, args, sh, world, barrier)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(case, edge, args.cpu_sample)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "edge": edge, "calls_per_step": ncalls,
+                           "ttm_precision": TTM_PRECISION_NAME.get(args.ttm_precision),
+                           "l2": "inputs larger than L2 (1 GiB per tensor); no flush",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "step_gbytes": wl.step_bytes / 1e9, "step_gflops": wl.step_flops / 1e9,
+                "roofline": roof, "breakdown": breakdown, "per_call": per_op_q,
+                "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def measure_e2e(tl, torch, wl, args, sh, world, barrier):
+    """Same step through the C ABI with inputs copied from pinned host memory
+    and every output copied back inside the timed region."""
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    hF, hL = pin(wl.memF), pin(wl.memL)
+    hb = [v.cpu().pin_memory() for v in wl.b]
+    hB = [m.cpu().pin_memory() for m in wl.B]
+    oV = torch.empty(wl.Cv.numel(), dtype=torch.float32).pin_memory()
+    oM = torch.empty(wl.Cm.numel(), dtype=torch.float32).pin_memory()
+    oE = torch.empty(wl.Ce.numel(), dtype=torch.float32).pin_memory()
+    h2d = hF.numel() * 4 + hL.numel() * 4 + sum(x.numel() * 4 for x in hb + hB)
+    d2h = 0
+    for c in wl.calls:
+        d2h += {"ttv": oV.numel(), "ttm": oM.numel(), "entrywise": oE.numel()}[c[0]] * 4
+
+    def step():
+        wl.AF.copy_(hF, non_blocking=True)
+        wl.AL.copy_(hL, non_blocking=True)
+        for d, h in zip(wl.b, hb):
+            d.copy_(h, non_blocking=True)
+        for d, h in zip(wl.B, hB):
+            d.copy_(h, non_blocking=True)
+        for c in wl.calls:
+            wl.run_call(c, sh)
+            if c[0] == "ttv":
+                oV.copy_(wl.Cv, non_blocking=True)
+            elif c[0] == "ttm":
+                oM.copy_(wl.Cm, non_blocking=True)
+            else:
+                oE.copy_(wl.Ce, non_blocking=True)
+
+    steps = max(2, min(args.steps, 5))
+    step()
+    torch.cuda.synchronize()
+    barrier()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(steps):
+        step()
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e)
+    if world > 1:
+        t = torch.tensor([ms], device=wl.dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return {"value": round(wl.step_bytes * world * steps / (ms / 1e3) / 1e9, 2), "unit": "GB/s",
+            "ms_per_step": round(ms / steps, 3), "steps": steps,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

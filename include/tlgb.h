@@ -1,0 +1,249 @@
+/*
+ * tlgb.h -- C ABI of the GB300-native (sm_103a) tensor-times-vector,
+ * tensor-times-matrix and entrywise library.
+ *
+ * The operations are those of Bassoy, "TLib: A Flexible C++ Tensor Framework
+ * for Numerical Tensor Calculus" (arXiv 1711.10912):
+ *   tl_ttv        mode-q tensor-times-vector, Sec. 5.2 Eq. 24
+ *   tl_ttm        mode-q tensor-times-matrix, Sec. 5.2 Eq. 25
+ *   tl_entrywise  layout-mixed entrywise ops, Sec. 5.1 Eqs. 22-23
+ *   tl_norm       Frobenius norm, Sec. 5.2 Table 3
+ * on dense or strided order-p tensors whose order p, extents n, layout tuple
+ * pi and strides w (Sec. 3.1 Eqs. 12-14, Sec. 3.2 Eq. 17) are runtime values.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Modes q and layout tuples pi are 1-based, as in the paper's equations;
+ *    multi-indices are 0-based with zero index offsets: `data` points at the
+ *    element with multi-index (0,...,0) (a view's first element, Eq. 18).
+ *  - Strides are in elements.  w == NULL derives the dense strides from pi by
+ *    Eq. 14; pi == NULL means the first-order layout (1,...,p) (Eq. 12).
+ *    Given strides must be >= 1; an output's strides must not make two of
+ *    its elements share an address.
+ *  - Extents n_r >= 1 (extent-1 modes are allowed and collapsed away).
+ *  - Every data pointer is DEVICE memory owned by the caller; the library
+ *    never frees it.  Descriptor arrays (n, pi, w) are host memory read
+ *    during the call only.
+ *  - Calls enqueue kernels on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and return without synchronising.  Argument errors are returned
+ *    synchronously and enqueue nothing.
+ *  - Outputs must not overlap any input (entrywise allows C == A or C == B
+ *    when the two descriptors are identical).
+ *  - Scratch memory: kernels that split a reduction across CTAs keep their
+ *    partial sums in a per-(device, stream) workspace owned by the library.
+ *    It is allocated (cudaMalloc) the first time a call on that stream needs
+ *    more than it holds, and reused afterwards; make one call of each shape
+ *    before capturing a stream into a CUDA graph.
+ *
+ * Return codes: TL_OK (0) or a negative TL_E* code; tl_strerror() names it.
+ */
+#ifndef TLGB_H
+#define TLGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TL_OK            0
+#define TL_EINVAL       -1   /* bad descriptor: p, q, pi not a permutation, shape mismatch */
+#define TL_EUNSUPPORTED -2   /* dtype / precision combination not offered */
+#define TL_ENOMEM       -3   /* admission or workspace allocation failed */
+#define TL_ECUDA        -4   /* a CUDA launch or runtime call failed */
+#define TL_ETIMEOUT     -5   /* a bounded device wait gave up */
+#define TL_ECANCELED    -6   /* request cancelled or failed by the host */
+#define TL_PENDING       1   /* tl_poll: the request has not completed yet */
+
+#define TL_MAX_ORDER 16
+
+/* element types of tensor data */
+#define TL_F32 0
+#define TL_F64 1
+
+/* compute precision of tl_ttm */
+#define TL_P_DEFAULT 0   /* the data type's own: FP32 or FP64 SIMT */
+#define TL_P_F64     1   /* FP64 data, FP64 arithmetic */
+#define TL_P_F32     2   /* FP32 data, FP32 FMA arithmetic */
+#define TL_P_TF32    3   /* FP32 data, TF32 tensor-core products, FP32 accumulation */
+#define TL_P_BF16    4   /* FP32 data rounded to BF16, FP32 accumulation */
+#define TL_P_BF16X3  5   /* FP32 data split into BF16 hi+lo, hi*hi+hi*lo+lo*hi, FP32 accumulation */
+
+/* entrywise operations (Sec. 5.1): C = A op B, COPY: C = A, SCALE: C = alpha*A */
+#define TL_ADD   0
+#define TL_SUB   1
+#define TL_MUL   2
+#define TL_DIV   3
+#define TL_COPY  4
+#define TL_SCALE 5
+
+/*
+ * Tensor descriptor: the (p, n, pi, w, data) description of Sec. 3.1-3.2.
+ * n[0..p-1] extents; pi[0..p-1] 1-based layout tuple or NULL; w[0..p-1]
+ * strides in elements or NULL; data = device address of element (0,...,0).
+ */
+typedef struct tl_tensor {
+    uint32_t       p;
+    int32_t        dtype;     /* TL_F32 or TL_F64 */
+    const int64_t* n;
+    const uint32_t* pi;
+    const int64_t* w;
+    void*          data;
+} tl_tensor;
+
+/*
+ * tl_ttv -- mode-q tensor-times-vector, Sec. 5.2 Eq. 24:
+ *   C(i_1..i_{q-1}, i_{q+1}..i_p) = sum_{k=0}^{n_q-1} A(i_1..k..i_p) * b(k)
+ * A: order p >= 2, any layout/strides.  b: device vector of n_q elements of
+ * A's dtype, element k at b[k*incb] (incb >= 1).  C: order p-1 with A's
+ * extents without mode q, same dtype, any layout/strides.
+ * accumulate = 0 overwrites C ('=' of Eq. 24); accumulate = 1 adds the sum
+ * to C's current value (the initial value of the paper's inner product).
+ * FP32 data accumulates in FP32, FP64 data in FP64.
+ * Errors: TL_EINVAL (p < 2, q outside 1..p, bad pi/w/extents, C's shape or
+ * dtype does not match), TL_ENOMEM (workspace), TL_ECUDA (launch).
+ */
+int tl_ttv(const tl_tensor* A, const void* b, int64_t incb, uint32_t q,
+           const tl_tensor* C, int32_t accumulate, void* stream);
+
+/*
+ * tl_ttm -- mode-q tensor-times-matrix, Sec. 5.2 Eq. 25:
+ *   C(i_1..j..i_p) = sum_{k=0}^{n_q-1} A(i_1..k..i_p) * B(j, k),  0 <= j < J
+ * B: device J x n_q matrix of A's dtype, B(j,k) at B[j*ldb_row + k*ldb_col]
+ * (row-major: ldb_row = n_q, ldb_col = 1).  C: A's extents with n_q
+ * replaced by J, same dtype, any layout/strides.  precision selects the
+ * arithmetic (TL_P_*); TF32, BF16 and BF16X3 need FP32 data and run on the
+ * tcgen05 tensor cores when the shape is dense enough (else they fall back
+ * to FP32 SIMT, which is at least as accurate).  accumulate as in tl_ttv.
+ * Errors: TL_EINVAL, TL_EUNSUPPORTED (precision not valid for the dtype),
+ * TL_ENOMEM, TL_ECUDA.
+ */
+int tl_ttm(const tl_tensor* A, const void* B, int64_t J, int64_t ldb_row, int64_t ldb_col,
+           uint32_t q, const tl_tensor* C, int32_t precision, int32_t accumulate,
+           void* stream);
+
+/*
+ * tl_entrywise -- Sec. 5.1 Eq. 23 (C(i) = A(i) op B(i)) and Eq. 22
+ * (C(i) = alpha * A(i)) over every multi-index i of A's shape; A, B and C
+ * may each have their own layout and strides (COPY with a different output
+ * layout is the paper's relayout, Sec. 3.2).  B must be NULL for COPY and
+ * SCALE and have A's shape and dtype otherwise.  alpha is used by SCALE only.
+ * Errors: TL_EINVAL, TL_ECUDA.
+ */
+int tl_entrywise(int32_t op, const tl_tensor* A, const tl_tensor* B, double alpha,
+                 const tl_tensor* C, void* stream);
+
+/*
+ * tl_norm -- Frobenius norm ||A||_F = sqrt(sum_i A(i)^2) (Table 3, norm),
+ * accumulated in FP64 with a deterministic two-pass block reduction.
+ * result: device pointer to three doubles, written asynchronously:
+ * {||A||_F, ||A||_F, 0} (the layout of tl_rel_error's result).
+ */
+int tl_norm(const tl_tensor* A, double* result, void* stream);
+
+/*
+ * tl_rel_error -- ||X - R||_F / ||R||_F over two tensors of equal shape
+ * (each in its own layout and dtype), in FP64 with the same deterministic
+ * reduction; the error measure the library's parity checks report.
+ * result: device pointer to three doubles {ratio, ||X-R||_F, ||R||_F}.
+ */
+int tl_rel_error(const tl_tensor* X, const tl_tensor* R, double* result, void* stream);
+
+/* Name of a return code. */
+const char* tl_strerror(int code);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int tl_version(void);
+
+/* Number of kernels this library has launched in this process (all devices,
+   all streams), for launch accounting in benchmarks. */
+uint64_t tl_launch_count(void);
+
+/*
+ * tl_plan_describe -- host-only: validates the arguments of a ttv (op 0),
+ * ttm (op 1) or entrywise (op 2) call exactly as the entry point would and
+ * writes a one-line JSON description of the collapsed iteration space and
+ * the kernel that would run into buf (NUL-terminated, truncated to buflen).
+ * Touches no GPU.  For ttm, `J` and `precision` are used; `entry_op` is the
+ * entrywise op.  Returns TL_OK or the error the entry point would return.
+ */
+int tl_plan_describe(int32_t op, const tl_tensor* A, const tl_tensor* B, uint32_t q,
+                     int64_t J, int32_t precision, int32_t entry_op,
+                     const tl_tensor* C, char* buf, size_t buflen);
+
+/* ------------------------------------------------------------------------
+ * Batched and served execution (no counterpart in the paper: these are the
+ * systems layers around the three operations above).
+ * ---------------------------------------------------------------------- */
+
+#define TL_OP_TTV       0
+#define TL_OP_TTM       1
+#define TL_OP_ENTRYWISE 2
+
+/*
+ * One operation of a batch: kind selects which fields are used.
+ *   TTV:       A, vec (b), incb, q, C, accumulate
+ *   TTM:       A, vec (B), J, ldb_row, ldb_col, q, C, precision, accumulate
+ *   ENTRYWISE: A, B (NULL-data for COPY/SCALE), C, entry_op, alpha
+ * Tensor descriptors and their arrays are copied at submission; data
+ * pointers must stay valid until the request completes.
+ */
+typedef struct tl_op {
+    int32_t   kind;
+    int32_t   entry_op;
+    int32_t   precision;
+    int32_t   accumulate;
+    uint32_t  q;
+    uint32_t  reserved;
+    int64_t   J, ldb_row, ldb_col, incb;
+    double    alpha;
+    const void* vec;
+    tl_tensor A, B, C;
+} tl_op;
+
+typedef struct tl_ctx tl_ctx;
+
+/* Context flags */
+#define TL_CTX_PERSISTENT 1   /* run batches through the persistent batched kernel */
+#define TL_CTX_GRAPH      2   /* replay the persistent launch from a CUDA graph */
+
+/*
+ * tl_ctx_create -- a request context on the current device: `budget_bytes`
+ * bounds the bytes of operands and outputs of requests admitted but not yet
+ * completed (requests beyond it wait; a single request larger than the
+ * budget is rejected with TL_ENOMEM), `streams` (>= 1) device streams carry
+ * concurrent batches.  The context owns its streams, descriptor tables and
+ * workspace and allocates them here.
+ */
+int tl_ctx_create(size_t budget_bytes, int32_t streams, int32_t flags, tl_ctx** out);
+int tl_ctx_destroy(tl_ctx* ctx);
+
+/*
+ * tl_batch_submit -- validates `count` operations and enqueues them as one
+ * request; returns at once with a ticket.  A request is admitted when the
+ * budget allows and a stream is free, then launched as one batch (one
+ * persistent launch, or one launch per operation without
+ * TL_CTX_PERSISTENT).  Errors: TL_EINVAL (the index of the first bad
+ * operation is not reported; use tl_plan_describe), TL_ENOMEM.
+ */
+int tl_batch_submit(tl_ctx* ctx, const tl_op* ops, size_t count, uint64_t* ticket);
+
+/*
+ * tl_poll -- non-blocking status of a ticket: *status = TL_PENDING, TL_OK or
+ * a negative error; *latency_ms = submission-to-completion time once done.
+ */
+int tl_poll(tl_ctx* ctx, uint64_t ticket, int32_t* status, double* latency_ms);
+
+/* Blocks until the ticket completes (or timeout_ms passes: TL_ETIMEOUT). */
+int tl_wait(tl_ctx* ctx, uint64_t ticket, double timeout_ms, int32_t* status,
+            double* latency_ms);
+
+/* Marks a pending, not yet launched request as cancelled (TL_ECANCELED). */
+int tl_cancel(tl_ctx* ctx, uint64_t ticket);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TLGB_H */

@@ -1,0 +1,369 @@
+// api.cpp -- the extern "C" entry points of tlgb.h: argument validation,
+// planning, workspace management and kernel dispatch.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+
+#include "kernels.h"
+#include "plan.h"
+#include "runtime.h"
+
+namespace tl {
+
+// ------------------------------------------------------------ device info ---
+
+int device_sms()
+{
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    cache[dev] = sms;
+    return sms;
+}
+
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+// -------------------------------------------------------------- workspace ---
+// One buffer per (device, stream), grown on demand and kept until exit.
+
+namespace {
+struct WsKey {
+    int dev;
+    uintptr_t stream;
+    bool operator<(const WsKey& o) const { return dev != o.dev ? dev < o.dev : stream < o.stream; }
+};
+struct WsBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+std::mutex g_ws_mu;
+std::map<WsKey, WsBuf> g_ws;
+}  // namespace
+
+void* workspace(cudaStream_t st, size_t bytes)
+{
+    if (bytes == 0) return nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    WsBuf& b = g_ws[WsKey{dev, reinterpret_cast<uintptr_t>(st)}];
+    if (b.bytes >= bytes) return b.ptr;
+    if (b.ptr) {
+        // the old buffer may still be read by work queued on this stream
+        if (cudaStreamSynchronize(st) != cudaSuccess) return nullptr;
+        cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+    }
+    size_t want = bytes < (size_t(1) << 20) ? (size_t(1) << 20) : bytes;
+    void* p = nullptr;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    b.ptr = p;
+    b.bytes = want;
+    return p;
+}
+
+// ---------------------------------------------------------------- overlap ---
+
+namespace {
+struct Range {
+    uintptr_t lo, hi;   // [lo, hi)
+};
+Range range_of(const Tensor& t)
+{
+    uintptr_t lo = reinterpret_cast<uintptr_t>(t.data);
+    return Range{lo, lo + (uintptr_t)t.span() * t.elem()};
+}
+Range range_of(const void* p, int64_t span, size_t elem)
+{
+    uintptr_t lo = reinterpret_cast<uintptr_t>(p);
+    return Range{lo, lo + (uintptr_t)span * elem};
+}
+bool overlaps(Range a, Range b) { return a.lo < b.hi && b.lo < a.hi; }
+bool same_desc(const Tensor& a, const Tensor& b)
+{
+    if (a.data != b.data || a.p != b.p || a.dtype != b.dtype) return false;
+    for (uint32_t r = 0; r < a.p; ++r)
+        if (a.n[r] != b.n[r] || a.w[r] != b.w[r]) return false;
+    return true;
+}
+}  // namespace
+
+// ----------------------------------------------------------- shared paths ---
+
+int prepare_ttv(const tl_tensor* A_, const void* b, int64_t incb, uint32_t q, const tl_tensor* C_,
+                int num_sms, Tensor& A, Tensor& C, TtvPlan& P)
+{
+    int rc = load_tensor(A_, false, A);
+    if (rc) return rc;
+    rc = load_tensor(C_, true, C);
+    if (rc) return rc;
+    if (!b) return TL_EINVAL;
+    rc = plan_ttv(A, incb, q, C, P, num_sms);
+    if (rc) return rc;
+    Range rc_ = range_of(C);
+    if (overlaps(rc_, range_of(A)) || overlaps(rc_, range_of(b, (P.nq - 1) * incb + 1, A.elem())))
+        return TL_EINVAL;
+    return TL_OK;
+}
+
+int prepare_ttm(const tl_tensor* A_, const void* B, int64_t J, int64_t ldb_row, int64_t ldb_col,
+                uint32_t q, const tl_tensor* C_, int32_t precision, Tensor& A, Tensor& C,
+                TtmPlan& P)
+{
+    int rc = load_tensor(A_, false, A);
+    if (rc) return rc;
+    rc = load_tensor(C_, true, C);
+    if (rc) return rc;
+    if (!B || ldb_row < 0 || ldb_col < 0) return TL_EINVAL;
+    rc = plan_ttm(A, J, ldb_row, ldb_col, q, C, precision, P);
+    if (rc) return rc;
+    Range rc_ = range_of(C);
+    int64_t bspan = (J - 1) * ldb_row + (P.nq - 1) * ldb_col + 1;
+    if (overlaps(rc_, range_of(A)) || overlaps(rc_, range_of(B, bspan, A.elem())))
+        return TL_EINVAL;
+    return TL_OK;
+}
+
+int prepare_entrywise(int32_t op, const tl_tensor* A_, const tl_tensor* B_, const tl_tensor* C_,
+                      Tensor& A, Tensor& B, Tensor& C, bool& hasB, EwPlan& P)
+{
+    int rc = load_tensor(A_, false, A);
+    if (rc) return rc;
+    rc = load_tensor(C_, true, C);
+    if (rc) return rc;
+    hasB = (B_ != nullptr);
+    if (hasB) {
+        rc = load_tensor(B_, false, B);
+        if (rc) return rc;
+    }
+    rc = plan_entrywise(op, A, hasB ? &B : nullptr, C, P);
+    if (rc) return rc;
+    Range rc_ = range_of(C);
+    if (overlaps(rc_, range_of(A)) && !same_desc(A, C)) return TL_EINVAL;
+    if (hasB && overlaps(rc_, range_of(B)) && !same_desc(B, C)) return TL_EINVAL;
+    return TL_OK;
+}
+
+int ttm_launches(const TtmPlan& P) { return P.kernel == K_TTM_TC ? ttm_tc_launches(P) : 1; }
+
+int run_ttm(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate, int sms,
+            cudaStream_t st)
+{
+    if (P.kernel == K_TTM_TC) return launch_ttm_tc(P, A, B, C, accumulate, sms, st);
+    return launch_ttm_simt(P, A, B, C, accumulate, sms, st);
+}
+
+}  // namespace tl
+
+using namespace tl;
+
+extern "C" {
+
+int tl_version(void) { return 100; }
+
+uint64_t tl_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* tl_strerror(int code)
+{
+    switch (code) {
+    case TL_OK: return "ok";
+    case TL_EINVAL: return "invalid argument";
+    case TL_EUNSUPPORTED: return "unsupported dtype/precision combination";
+    case TL_ENOMEM: return "out of memory or over the admission budget";
+    case TL_ECUDA: return "CUDA error";
+    case TL_ETIMEOUT: return "device wait timed out";
+    case TL_ECANCELED: return "request cancelled";
+    case TL_PENDING: return "pending";
+    default: return "unknown error";
+    }
+}
+
+int tl_ttv(const tl_tensor* A_, const void* b, int64_t incb, uint32_t q, const tl_tensor* C_,
+           int32_t accumulate, void* stream)
+{
+    Tensor A, C;
+    TtvPlan P;
+    int sms = device_sms();
+    if (sms <= 0) return TL_ECUDA;
+    int rc = prepare_ttv(A_, b, incb, q, C_, sms, A, C, P);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* ws = nullptr;
+    size_t wb = ttv_workspace_bytes(P);
+    if (wb) {
+        ws = workspace(st, wb);
+        if (!ws) return TL_ENOMEM;
+    }
+    rc = launch_ttv(P, A.data, b, C.data, ws, accumulate ? 1 : 0, sms, st);
+    if (rc == TL_OK) count_launches(P.splits > 1 ? 2 : 1);
+    return rc;
+}
+
+int tl_ttm(const tl_tensor* A_, const void* B, int64_t J, int64_t ldb_row, int64_t ldb_col,
+           uint32_t q, const tl_tensor* C_, int32_t precision, int32_t accumulate, void* stream)
+{
+    Tensor A, C;
+    TtmPlan P;
+    int sms = device_sms();
+    if (sms <= 0) return TL_ECUDA;
+    int rc = prepare_ttm(A_, B, J, ldb_row, ldb_col, q, C_, precision, A, C, P);
+    if (rc) return rc;
+    rc = run_ttm(P, A.data, B, C.data, accumulate ? 1 : 0, sms, static_cast<cudaStream_t>(stream));
+    if (rc == TL_OK) count_launches(ttm_launches(P));
+    return rc;
+}
+
+int tl_entrywise(int32_t op, const tl_tensor* A_, const tl_tensor* B_, double alpha,
+                 const tl_tensor* C_, void* stream)
+{
+    Tensor A, B, C;
+    EwPlan P;
+    bool hasB = false;
+    int sms = device_sms();
+    if (sms <= 0) return TL_ECUDA;
+    int rc = prepare_entrywise(op, A_, B_, C_, A, B, C, hasB, P);
+    if (rc) return rc;
+    rc = launch_entrywise(P, A.data, hasB ? B.data : nullptr, alpha, C.data, sms,
+                          static_cast<cudaStream_t>(stream));
+    if (rc == TL_OK && P.N > 0) count_launches(1);
+    return rc;
+}
+
+static int norm_common(const Tensor& X, const Tensor* R, double* result, cudaStream_t st)
+{
+    Space sp;
+    sp.nops = 2;
+    for (uint32_t r = 0; r < X.p; ++r) {
+        Dim& d = sp.d[sp.nd++];
+        d.n = X.n[r];
+        d.s[0] = X.w[r];
+        d.s[1] = R ? R->w[r] : 0;
+        d.s[2] = 0;
+    }
+    collapse(sp, 0);
+    int nb = norm_partial_blocks(sp.count(), device_sms());
+    double* partials = static_cast<double*>(workspace(st, sizeof(double) * 2 * (size_t)nb));
+    if (!partials) return TL_ENOMEM;
+    int rc = launch_norm(sp, X.dtype, X.data, R ? R->dtype : X.dtype, R ? R->data : nullptr,
+                         partials, nb, result, st);
+    if (rc == TL_OK) count_launches(2);
+    return rc;
+}
+
+int tl_norm(const tl_tensor* A_, double* result, void* stream)
+{
+    Tensor A;
+    int rc = load_tensor(A_, false, A);
+    if (rc) return rc;
+    if (!result) return TL_EINVAL;
+    return norm_common(A, nullptr, result, static_cast<cudaStream_t>(stream));
+}
+
+int tl_rel_error(const tl_tensor* X_, const tl_tensor* R_, double* result, void* stream)
+{
+    Tensor X, R;
+    int rc = load_tensor(X_, false, X);
+    if (rc) return rc;
+    rc = load_tensor(R_, false, R);
+    if (rc) return rc;
+    if (!result || X.p != R.p) return TL_EINVAL;
+    for (uint32_t r = 0; r < X.p; ++r)
+        if (X.n[r] != R.n[r]) return TL_EINVAL;
+    return norm_common(X, &R, result, static_cast<cudaStream_t>(stream));
+}
+
+static void append_space(std::string& s, const Space& sp)
+{
+    s += "[";
+    for (int i = 0; i < sp.nd; ++i) {
+        char b[128];
+        std::snprintf(b, sizeof b, "%s[%lld", i ? "," : "", (long long)sp.d[i].n);
+        s += b;
+        for (int o = 0; o < sp.nops; ++o) {
+            std::snprintf(b, sizeof b, ",%lld", (long long)sp.d[i].s[o]);
+            s += b;
+        }
+        s += "]";
+    }
+    s += "]";
+}
+
+int tl_plan_describe(int32_t op, const tl_tensor* A_, const tl_tensor* B_, uint32_t q, int64_t J,
+                     int32_t precision, int32_t entry_op, const tl_tensor* C_, char* buf,
+                     size_t buflen)
+{
+    const int kSms = 152;   // planning assumes a full GB300 when no GPU is queried
+    std::string s;
+    char b[512];
+    int rc;
+    if (op == TL_OP_TTV) {
+        Tensor A, C;
+        TtvPlan P;
+        static const float dummy[1] = {0.f};
+        rc = prepare_ttv(A_, dummy, 1, q, C_, kSms, A, C, P);
+        if (rc) return rc;
+        std::snprintf(b, sizeof b,
+                      "{\"op\":\"ttv\",\"kernel\":\"%s\",\"nq\":%lld,\"saq\":%lld,\"nout\":%lld,"
+                      "\"vec\":%d,\"lanes\":%d,\"splits\":%d,\"kchunk\":%lld,\"dims\":",
+                      kernel_name(P.kernel), (long long)P.nq, (long long)P.saq,
+                      (long long)P.nout, P.vec, P.lanes, P.splits, (long long)P.kchunk);
+        s = b;
+        append_space(s, P.out);
+        s += "}";
+    } else if (op == TL_OP_TTM) {
+        Tensor A, C;
+        TtmPlan P;
+        static const float dummy[1] = {0.f};
+        rc = prepare_ttm(A_, dummy, J, 0, 0, q, C_, precision, A, C, P);
+        if (rc) return rc;
+        std::snprintf(b, sizeof b,
+                      "{\"op\":\"ttm\",\"kernel\":\"%s\",\"precision\":%d,\"nq\":%lld,"
+                      "\"saq\":%lld,\"J\":%lld,\"scq\":%lld,\"M\":%lld,\"tc_variant\":%d,"
+                      "\"dims\":",
+                      kernel_name(P.kernel), P.precision, (long long)P.nq, (long long)P.saq,
+                      (long long)P.J, (long long)P.scq, (long long)P.M, P.tc_variant);
+        s = b;
+        append_space(s, P.rows);
+        s += "}";
+    } else if (op == TL_OP_ENTRYWISE) {
+        Tensor A, B, C;
+        EwPlan P;
+        bool hasB = false;
+        rc = prepare_entrywise(entry_op, A_, B_, C_, A, B, C, hasB, P);
+        if (rc) return rc;
+        std::snprintf(b, sizeof b,
+                      "{\"op\":\"entrywise\",\"kernel\":\"%s\",\"N\":%lld,\"vec\":%d,"
+                      "\"tdim\":%d,\"dims\":",
+                      kernel_name(P.kernel), (long long)P.N, P.vec, P.tdim);
+        s = b;
+        append_space(s, P.sp);
+        s += "}";
+    } else {
+        return TL_EINVAL;
+    }
+    if (buf && buflen) {
+        std::strncpy(buf, s.c_str(), buflen - 1);
+        buf[buflen - 1] = '\0';
+    }
+    return TL_OK;
+}
+
+}  // extern "C"

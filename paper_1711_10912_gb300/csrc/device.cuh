@@ -1,0 +1,107 @@
+// device.cuh -- small device helpers shared by the kernels: the offset mapper
+// (linear index -> per-operand element offsets, the layout function of Sec. 3.2
+// Eq. 17 applied to a collapsed iteration space) and 16-byte vector types.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "plan.h"
+
+namespace tl {
+
+// Collapsed iteration space as kernel parameters: dims[0] varies fastest.
+struct DevSpace {
+    int nd;
+    int64_t n[kMaxDims];
+    int64_t s[3][kMaxDims];
+};
+
+inline DevSpace to_dev(const Space& sp)
+{
+    DevSpace d{};
+    d.nd = sp.nd;
+    for (int i = 0; i < sp.nd; ++i) {
+        d.n[i] = sp.d[i].n;
+        for (int o = 0; o < 3; ++o) d.s[o][i] = sp.d[i].s[o];
+    }
+    return d;
+}
+
+// Offsets of linear index g for operands 0..NOPS-1.  dim 0 is taken in units
+// of `vec0` elements (g counts vectors along dim 0); the last dim needs no
+// division because g is already below its extent.
+template <int NOPS>
+__device__ __forceinline__ void map_offsets(const DevSpace& sp, int64_t g, int64_t vec0,
+                                            int64_t* off)
+{
+#pragma unroll
+    for (int o = 0; o < NOPS; ++o) off[o] = 0;
+    for (int d = 0; d < sp.nd; ++d) {
+        int64_t ext = d == 0 ? sp.n[0] / vec0 : sp.n[d];
+        int64_t i;
+        if (d == sp.nd - 1) {
+            i = g;
+        } else {
+            int64_t qd = g / ext;
+            i = g - qd * ext;
+            g = qd;
+        }
+        if (d == 0) i *= vec0;
+#pragma unroll
+        for (int o = 0; o < NOPS; ++o) off[o] += i * sp.s[o][d];
+    }
+}
+
+template <typename T, int V> struct Vec;
+template <> struct Vec<float, 4> { using type = float4; };
+template <> struct Vec<float, 2> { using type = float2; };
+template <> struct Vec<float, 1> { using type = float; };
+template <> struct Vec<double, 2> { using type = double2; };
+template <> struct Vec<double, 1> { using type = double; };
+
+template <typename T, int V>
+__device__ __forceinline__ void vload(const T* p, T* r)
+{
+    if constexpr (V == 1) {
+        r[0] = __ldg(p);
+    } else {
+        using VT = typename Vec<T, V>::type;
+        VT v = __ldg(reinterpret_cast<const VT*>(p));
+        const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+        for (int i = 0; i < V; ++i) r[i] = e[i];
+    }
+}
+
+// Streaming load: read-once data that should not displace L1 lines.
+template <typename T, int V>
+__device__ __forceinline__ void vload_stream(const T* p, T* r)
+{
+    if constexpr (V == 1) {
+        r[0] = __ldcs(p);
+    } else {
+        using VT = typename Vec<T, V>::type;
+        VT v = __ldcs(reinterpret_cast<const VT*>(p));
+        const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+        for (int i = 0; i < V; ++i) r[i] = e[i];
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void vstore(T* p, const T* r)
+{
+    if constexpr (V == 1) {
+        p[0] = r[0];
+    } else {
+        using VT = typename Vec<T, V>::type;
+        VT v;
+        T* e = reinterpret_cast<T*>(&v);
+#pragma unroll
+        for (int i = 0; i < V; ++i) e[i] = r[i];
+        *reinterpret_cast<VT*>(p) = v;
+    }
+}
+
+}  // namespace tl

@@ -1,0 +1,36 @@
+// kernels.h -- launchers of the CUDA kernels, called by the C ABI (api.cpp).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace tl {
+
+size_t ttv_workspace_bytes(const TtvPlan& P);
+int launch_ttv(const TtvPlan& P, const void* A, const void* b, void* C, void* ws,
+               int accumulate, int num_sms, cudaStream_t st);
+
+int launch_entrywise(const EwPlan& P, const void* A, const void* B, double alpha, void* C,
+                     int num_sms, cudaStream_t st);
+
+int launch_ttm_simt(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate,
+                    int num_sms, cudaStream_t st);
+
+// Deterministic FP64 sum-of-squares reduction over a collapsed space with
+// operand 0 = X (dtype dx) and, when R != nullptr, operand 1 = R (dtype dr):
+// writes {sqrt(num/den), sqrt(num), sqrt(den)} with num = sum (x-r)^2 and
+// den = sum r^2 (R == nullptr: num = sum x^2, den = 0, result[0] = sqrt(num)).
+// partials must hold 2 * norm_partial_blocks(...) doubles.
+int norm_partial_blocks(int64_t count, int num_sms);
+int launch_norm(const Space& sp, int dx, const void* X, int dr, const void* R, double* partials,
+                int nblocks, double* result, cudaStream_t st);
+
+}  // namespace tl
+
+namespace tl {
+int launch_ttm_tc(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate,
+                  int num_sms, cudaStream_t st);
+// kernels one launch_ttm_tc call enqueues
+int ttm_tc_launches(const TtmPlan& P);
+}  // namespace tl

@@ -1,0 +1,28 @@
+// runtime.h -- shared host-side pieces of the C ABI: device properties, the
+// per-stream workspace and the validated "prepare" step of each operation
+// (used by the direct entry points and by the batch / serving runtime).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace tl {
+
+int device_sms();
+// Adds n to the process-wide launch counter reported by tl_launch_count().
+void count_launches(int n);
+void* workspace(cudaStream_t st, size_t bytes);
+
+int prepare_ttv(const tl_tensor* A, const void* b, int64_t incb, uint32_t q, const tl_tensor* C,
+                int num_sms, Tensor& At, Tensor& Ct, TtvPlan& P);
+int prepare_ttm(const tl_tensor* A, const void* B, int64_t J, int64_t ldb_row, int64_t ldb_col,
+                uint32_t q, const tl_tensor* C, int32_t precision, Tensor& At, Tensor& Ct,
+                TtmPlan& P);
+int prepare_entrywise(int32_t op, const tl_tensor* A, const tl_tensor* B, const tl_tensor* C,
+                      Tensor& At, Tensor& Bt, Tensor& Ct, bool& hasB, EwPlan& P);
+int ttm_launches(const TtmPlan& P);
+int run_ttm(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate, int sms,
+            cudaStream_t st);
+
+}  // namespace tl

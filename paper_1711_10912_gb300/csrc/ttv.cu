@@ -1,0 +1,270 @@
+// ttv.cu -- mode-q tensor-times-vector, Sec. 5.2 Eq. 24:
+//   C(i without q) = sum_{k < n_q} A(i with i_q = k) * b(k).
+//
+// After collapsing (plan.cpp) the output modes form a space whose dim 0 is
+// the output mode with the smallest stride in A.  Two kernels cover every
+// layout:
+//   ttv_row  the contracted mode is contiguous in A (w_q = 1, the paper's
+//            "m = 0" special case of Sec. 5.2): a group of L lanes reads one
+//            output's fiber with 16-byte loads and reduces it by warp
+//            shuffles; each group keeps R fibers in flight.
+//   ttv_col  the contracted mode is strided: threads run along the output
+//            dims (coalesced when dim 0 is contiguous in A), each thread walks
+//            k with stride w_q and keeps VEC sums in registers.
+// When the outputs alone cannot fill the GPU, the k range is split across
+// CTAs; each split writes FP partial sums to the workspace and a second
+// kernel adds them in split order (deterministic).
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace tl {
+
+namespace {
+
+struct TtvArgs {
+    const void* A;
+    const void* b;
+    void* C;
+    void* ws;
+    DevSpace out;       // operands 0 = A, 1 = C
+    int64_t nq, saq, incb, nout, kchunk;
+    int splits, accumulate;
+};
+
+constexpr int kThreads = 256;
+
+template <typename T, int VEC, int L, int R>
+__global__ void __launch_bounds__(kThreads) ttv_row_kernel(const TtvArgs a)
+{
+    const T* __restrict__ A = static_cast<const T*>(a.A);
+    const T* __restrict__ b = static_cast<const T*>(a.b);
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % L;
+    const int64_t group = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / L;
+    const int64_t ngroups = (int64_t)gridDim.x * kThreads / L;
+    const int64_t work = a.nout * a.splits;
+    // every lane of a warp runs the same number of iterations so the
+    // shuffles below always see a converged warp
+    const int64_t iters = (work + (int64_t)R * ngroups - 1) / ((int64_t)R * ngroups);
+    for (int64_t it = 0; it < iters; ++it) {
+        T acc[R];
+        int64_t item[R], offA[R];
+        bool ok[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            item[r] = (it * R + r) * ngroups + group;
+            ok[r] = item[r] < work;
+            acc[r] = T(0);
+            offA[r] = 0;
+        }
+        int64_t k0[R], k1[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int64_t row = ok[r] ? item[r] % a.nout : 0;
+            int64_t s = ok[r] ? item[r] / a.nout : 0;
+            int64_t off[2];
+            map_offsets<1>(a.out, row, 1, off);
+            offA[r] = off[0];
+            k0[r] = s * a.kchunk;
+            k1[r] = ok[r] ? min(a.nq, k0[r] + a.kchunk) : k0[r];
+        }
+        // all rows of this iteration share the same k extent except at the
+        // last split; walk the longest and guard per row
+        int64_t kspan = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) kspan = max(kspan, k1[r] - k0[r]);
+        for (int64_t kk = (int64_t)sub * VEC; kk < kspan; kk += (int64_t)L * VEC) {
+            T va[R][VEC];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (kk < k1[r] - k0[r]) {
+                    vload_stream<T, VEC>(A + offA[r] + k0[r] + kk, va[r]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) va[r][v] = T(0);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (kk < k1[r] - k0[r]) {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v)
+                        acc[r] = fma(va[r][v], __ldg(b + (k0[r] + kk + v) * a.incb), acc[r]);
+                }
+            }
+        }
+        // scalar tail when VEC == 1 handled by the loop; reduce within groups
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+#pragma unroll
+            for (int m = L / 2; m >= 1; m /= 2) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], m);
+        }
+        if (sub == 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (!ok[r]) continue;
+                int64_t row = item[r] % a.nout;
+                int64_t s = item[r] / a.nout;
+                if (a.splits > 1) {
+                    static_cast<T*>(a.ws)[s * a.nout + row] = acc[r];
+                } else {
+                    int64_t off[2];
+                    map_offsets<2>(a.out, row, 1, off);
+                    T* c = static_cast<T*>(a.C) + off[1];
+                    *c = a.accumulate ? *c + acc[r] : acc[r];
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int VEC, int U>
+__global__ void __launch_bounds__(kThreads) ttv_col_kernel(const TtvArgs a)
+{
+    const T* __restrict__ A = static_cast<const T*>(a.A);
+    const T* __restrict__ b = static_cast<const T*>(a.b);
+    const int64_t items = a.nout / VEC;
+    const int64_t work = items * a.splits;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < work; t += stride) {
+        const int64_t g = t % items;
+        const int64_t s = t / items;
+        int64_t off[2];
+        map_offsets<2>(a.out, g, VEC, off);
+        const int64_t k0 = s * a.kchunk;
+        const int64_t k1 = min(a.nq, k0 + a.kchunk);
+        T acc[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] = T(0);
+        const T* pa = A + off[0];
+        int64_t k = k0;
+        for (; k + U <= k1; k += U) {
+            T va[U][VEC];
+            T vb[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                vload_stream<T, VEC>(pa + (k + u) * a.saq, va[u]);
+                vb[u] = __ldg(b + (k + u) * a.incb);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[v] = fma(va[u][v], vb[u], acc[v]);
+        }
+        for (; k < k1; ++k) {
+            T va[VEC];
+            vload_stream<T, VEC>(pa + k * a.saq, va);
+            T bk = __ldg(b + k * a.incb);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[v] = fma(va[v], bk, acc[v]);
+        }
+        if (a.splits > 1) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) static_cast<T*>(a.ws)[s * a.nout + g * VEC + v] = acc[v];
+        } else {
+            T* pc = static_cast<T*>(a.C) + off[1];
+            if (a.accumulate) {
+                T old[VEC];
+                if (VEC > 1) vload<T, VEC>(pc, old);
+                else old[0] = *pc;
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[v] += old[v];
+            }
+            vstore<T, VEC>(pc, acc);
+        }
+    }
+}
+
+// Adds the split partial sums ws[s][e] in split order and writes C.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) ttv_splitk_reduce(const TtvArgs a)
+{
+    const T* ws = static_cast<const T*>(a.ws);
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < a.nout; e += stride) {
+        T sum = T(0);
+        for (int s = 0; s < a.splits; ++s) sum += ws[(int64_t)s * a.nout + e];
+        int64_t off[2];
+        map_offsets<2>(a.out, e, 1, off);
+        T* c = static_cast<T*>(a.C) + off[1];
+        *c = a.accumulate ? *c + sum : sum;
+    }
+}
+
+int grid_for(int64_t threads, int num_sms)
+{
+    int64_t blocks = (threads + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)num_sms * (2048 / kThreads);
+    if (blocks > cap) blocks = cap;
+    return (int)(blocks < 1 ? 1 : blocks);
+}
+
+template <typename T>
+int launch_typed(const TtvPlan& P, const void* A, const void* b, void* C, void* ws,
+                 int accumulate, int num_sms, cudaStream_t st)
+{
+    TtvArgs a{};
+    a.A = A;
+    a.b = b;
+    a.C = C;
+    a.ws = ws;
+    a.out = to_dev(P.out);
+    a.nq = P.nq;
+    a.saq = P.saq;
+    a.incb = P.incb;
+    a.nout = P.nout;
+    a.kchunk = P.kchunk;
+    a.splits = P.splits;
+    a.accumulate = accumulate;
+    constexpr int V = 16 / sizeof(T);
+    if (P.kernel == K_TTV_ROW) {
+        constexpr int R = 4;
+        int64_t threads = (P.nout * P.splits + R - 1) / R * P.lanes;
+        int grid = grid_for(threads, num_sms);
+#define TL_ROW(VV, LL) ttv_row_kernel<T, VV, LL, R><<<grid, kThreads, 0, st>>>(a)
+        if (P.vec == V) {
+            switch (P.lanes) {
+            case 32: TL_ROW(V, 32); break;
+            case 16: TL_ROW(V, 16); break;
+            case 8: TL_ROW(V, 8); break;
+            default: TL_ROW(V, 4); break;
+            }
+        } else {
+            switch (P.lanes) {
+            case 32: TL_ROW(1, 32); break;
+            case 16: TL_ROW(1, 16); break;
+            case 8: TL_ROW(1, 8); break;
+            default: TL_ROW(1, 4); break;
+            }
+        }
+#undef TL_ROW
+    } else {
+        int64_t threads = P.nout / P.vec * P.splits;
+        int grid = grid_for(threads, num_sms);
+        if (P.vec == V) ttv_col_kernel<T, V, 4><<<grid, kThreads, 0, st>>>(a);
+        else ttv_col_kernel<T, 1, 4><<<grid, kThreads, 0, st>>>(a);
+    }
+    if (P.splits > 1) {
+        ttv_splitk_reduce<T><<<grid_for(P.nout, num_sms), kThreads, 0, st>>>(a);
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
+}
+
+}  // namespace
+
+size_t ttv_workspace_bytes(const TtvPlan& P)
+{
+    if (P.splits <= 1) return 0;
+    return (size_t)P.splits * (size_t)P.nout * (P.dtype == TL_F64 ? 8 : 4);
+}
+
+int launch_ttv(const TtvPlan& P, const void* A, const void* b, void* C, void* ws,
+               int accumulate, int num_sms, cudaStream_t st)
+{
+    if (P.dtype == TL_F64) return launch_typed<double>(P, A, b, C, ws, accumulate, num_sms, st);
+    return launch_typed<float>(P, A, b, C, ws, accumulate, num_sms, st);
+}
+
+}  // namespace tl

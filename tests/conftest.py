@@ -29,8 +29,9 @@ def ints(s):
 def tl():
     """The CUDA library's Python binding (built in-tree on first use)."""
     from paper_1711_10912_gb300 import build as _build
-    _build.build()
     import paper_1711_10912_gb300 as tlmod
+    _build.build()
+    tlmod.load_library()
     return tlmod
 
 

@@ -1,0 +1,167 @@
+"""Host-only checks of the C-ABI library (no GPU): every symbol declared in
+include/tlgb.h is exported, argument validation returns the documented codes,
+and the planner's collapsed iteration space enumerates exactly the element
+pairs of the uncollapsed description."""
+import itertools
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from conftest import ROOT
+
+FAKE = 1 << 20          # a non-null, 16-byte aligned fake device address
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "tlgb.h")) as fh:
+        src = fh.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tl_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_documented_entry_points():
+    names = declared_functions()
+    for must in ("tl_ttv", "tl_ttm", "tl_entrywise", "tl_batch_submit", "tl_poll",
+                 "tl_norm", "tl_strerror", "tl_ctx_create"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(tl):
+    for name in declared_functions():
+        assert hasattr(tl._lib, name), f"{name} not exported by libtlgb.so"
+
+
+def test_strerror_and_version(tl):
+    assert tl.tl_version() >= 100
+    assert tl.tl_strerror(tl.TL_EINVAL) == "invalid argument"
+    assert tl.tl_strerror(12345) == "unknown error"
+
+
+def _desc(tl, n, pi=None, w=None, dtype="f32", addr=FAKE):
+    return tl.Desc(addr, n, pi, w, dtype=dtype)
+
+
+def _plan(tl, op, A, C, q=0, B=None, J=0, prec=0, eop=0):
+    rc, js = tl.tl_plan_describe(op, A, B, q, J, prec, eop, C)
+    return rc, (json.loads(js) if rc == 0 else None)
+
+
+def test_plan_config2_kernels(tl):
+    n = (128,) * 4
+    for pi, q, kern, dims in [
+        ((1, 2, 3, 4), 1, "ttv_row", [[128 ** 3, 128, 1]]),
+        ((1, 2, 3, 4), 2, "ttv_col", [[128, 1, 1], [128 ** 2, 128 ** 2, 128]]),
+        ((1, 2, 3, 4), 4, "ttv_col", [[128 ** 3, 1, 1]]),
+        ((4, 3, 2, 1), 4, "ttv_row", [[128 ** 3, 128, 1]]),
+    ]:
+        A = _desc(tl, n, pi)
+        nout = tuple(x for r, x in enumerate(n) if r != q - 1)
+        pic = tuple(r for r in pi if r != q)
+        pic = tuple(sorted(pic).index(r) + 1 for r in pic)   # induced layout
+        C = _desc(tl, nout, pic, addr=FAKE * 2 ** 12)
+        rc, P = _plan(tl, tl.TL_OP_TTV, A, C, q=q)
+        assert rc == 0
+        assert P["kernel"] == kern
+        assert P["dims"] == dims
+        assert P["splits"] == 1
+        assert P["vec"] == 4
+
+
+def _enumerate_pairs(space, nops):
+    """All per-operand offset tuples of a collapsed space."""
+    out = set()
+    exts = [d[0] for d in space]
+    for idx in itertools.product(*[range(e) for e in exts]):
+        out.add(tuple(sum(i * d[1 + o] for i, d in zip(idx, space)) for o in range(nops)))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_collapse_preserves_element_pairs_ttv(tl, seed):
+    g = synth.rng(700 + seed)
+    p = int(g.integers(2, 6))
+    n = tuple(int(x) for x in g.integers(1, 5, size=p))
+    q = int(g.integers(1, p + 1))
+    pa = synth.random_layout(p, g)
+    nout = tuple(x for r, x in enumerate(n) if r != q - 1)
+    pc = synth.random_layout(p - 1, g)
+    wA, wC = oracle.strides(n, pa), oracle.strides(nout, pc)
+    rc, P = _plan(tl, tl.TL_OP_TTV, _desc(tl, n, pa), _desc(tl, nout, pc, addr=FAKE * 4096), q=q)
+    assert rc == 0
+    assert P["nq"] == n[q - 1] and P["saq"] == wA[q - 1]
+    expect = set()
+    for i in itertools.product(*[range(x) for x in nout]):
+        full = list(i)
+        full.insert(q - 1, 0)
+        expect.add((oracle.lam(wA, full), oracle.lam(wC, i)))
+    assert _enumerate_pairs(P["dims"], 2) == expect
+    assert P["nout"] == int(np.prod(nout))
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_collapse_preserves_element_triples_entrywise(tl, seed):
+    g = synth.rng(800 + seed)
+    p = int(g.integers(1, 6))
+    n = tuple(int(x) for x in g.integers(1, 5, size=p))
+    pa, pb, pc = (synth.random_layout(p, g) for _ in range(3))
+    w = [oracle.strides(n, pi) for pi in (pa, pb, pc)]
+    rc, P = _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, n, pa), _desc(tl, n, pc, addr=FAKE * 4096),
+                  B=_desc(tl, n, pb, addr=FAKE * 8192), eop=tl.TL_ADD)
+    assert rc == 0
+    expect = {tuple(oracle.lam(wx, i) for wx in w)
+              for i in itertools.product(*[range(x) for x in n])}
+    got = _enumerate_pairs(P["dims"], 3) if P["dims"] else {(0, 0, 0)}
+    assert got == expect
+
+
+def test_entrywise_kernel_choice(tl):
+    n = (64, 64, 64)
+    F, L = (1, 2, 3), (3, 2, 1)
+    for pa, pb, pc, kern in [(F, F, F, "ew_flat"), (F, L, F, "ew_tile"), (L, F, F, "ew_tile"),
+                             (L, L, L, "ew_flat")]:
+        rc, P = _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, n, pa), _desc(tl, n, pc, addr=FAKE * 4096),
+                      B=_desc(tl, n, pb, addr=FAKE * 8192), eop=tl.TL_ADD)
+        assert rc == 0 and P["kernel"] == kern
+
+
+def test_validation_errors(tl):
+    n = (4, 5, 6)
+    A = _desc(tl, n)
+    C = _desc(tl, (4, 6), addr=FAKE * 4096)
+    assert _plan(tl, tl.TL_OP_TTV, A, C, q=2)[0] == 0
+    assert _plan(tl, tl.TL_OP_TTV, A, C, q=0)[0] == tl.TL_EINVAL
+    assert _plan(tl, tl.TL_OP_TTV, A, C, q=4)[0] == tl.TL_EINVAL
+    assert _plan(tl, tl.TL_OP_TTV, A, C, q=1)[0] == tl.TL_EINVAL       # wrong output shape
+    assert _plan(tl, tl.TL_OP_TTV, _desc(tl, n, (1, 1, 2)), C, q=2)[0] == tl.TL_EINVAL
+    assert _plan(tl, tl.TL_OP_TTV, _desc(tl, (4,)), _desc(tl, (1,), addr=FAKE * 4096), q=1)[0] \
+        == tl.TL_EINVAL                                                 # p < 2
+    assert _plan(tl, tl.TL_OP_TTV, A, _desc(tl, (4, 6), dtype="f64", addr=FAKE * 4096),
+                 q=2)[0] == tl.TL_EINVAL                                # dtype mismatch
+    assert _plan(tl, tl.TL_OP_TTV, A, _desc(tl, (4, 6), addr=FAKE), q=2)[0] == tl.TL_EINVAL
+    assert _plan(tl, tl.TL_OP_TTV, A, _desc(tl, (4, 6), w=(1, 2), addr=FAKE * 4096),
+                 q=2)[0] == tl.TL_EINVAL                                # self-overlapping C
+    assert _plan(tl, tl.TL_OP_TTV, _desc(tl, n, w=(1, 0, 3)), C, q=2)[0] == tl.TL_EINVAL
+    # ttm
+    Cm = _desc(tl, (4, 3, 6), addr=FAKE * 4096)
+    assert _plan(tl, tl.TL_OP_TTM, A, Cm, q=2, J=3)[0] == 0
+    assert _plan(tl, tl.TL_OP_TTM, A, Cm, q=2, J=4)[0] == tl.TL_EINVAL
+    assert _plan(tl, tl.TL_OP_TTM, A, Cm, q=2, J=3, prec=tl.TL_P_F64)[0] == tl.TL_EUNSUPPORTED
+    Ad = _desc(tl, n, dtype="f64")
+    Cd = _desc(tl, (4, 3, 6), dtype="f64", addr=FAKE * 4096)
+    assert _plan(tl, tl.TL_OP_TTM, Ad, Cd, q=2, J=3, prec=tl.TL_P_BF16X3)[0] == tl.TL_EUNSUPPORTED
+    assert _plan(tl, tl.TL_OP_TTM, Ad, Cd, q=2, J=3, prec=9)[0] == tl.TL_EINVAL
+    # entrywise: B required for binary ops, forbidden for unary ones
+    Ce = _desc(tl, n, addr=FAKE * 4096)
+    assert _plan(tl, tl.TL_OP_ENTRYWISE, A, Ce, eop=tl.TL_ADD)[0] == tl.TL_EINVAL
+    assert _plan(tl, tl.TL_OP_ENTRYWISE, A, Ce, B=_desc(tl, n), eop=tl.TL_COPY)[0] == tl.TL_EINVAL
+    assert _plan(tl, tl.TL_OP_ENTRYWISE, A, Ce, eop=tl.TL_COPY)[0] == 0
+    # in place with identical descriptors is allowed, with another layout it is not
+    assert _plan(tl, tl.TL_OP_ENTRYWISE, A, _desc(tl, n), B=_desc(tl, n, addr=FAKE * 8192),
+                 eop=tl.TL_ADD)[0] == 0
+    assert _plan(tl, tl.TL_OP_ENTRYWISE, A, _desc(tl, n, (3, 2, 1)),
+                 B=_desc(tl, n, addr=FAKE * 8192), eop=tl.TL_ADD)[0] == tl.TL_EINVAL

@@ -1,0 +1,110 @@
+"""GPU parity of tl_entrywise (Sec. 5.1 Eqs. 22-23) against the FP64 oracle.
+
+A single +, -, *, / of FP32 (FP64) operands is correctly rounded on the GPU,
+and rounding the oracle's FP64 result to FP32 gives the same correctly rounded
+value (53 >= 2*24 + 2 bits, so the double rounding is innocuous), so every
+comparison here is bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import NP, get, put, to_dev
+
+pytestmark = pytest.mark.gpu
+
+OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "copy": 4, "scale": 5}
+
+
+def ew_case(tl, dev, op, X, Y, pa, pb, pc, dtype, alpha=-1.5):
+    n = X.shape
+    Xd = np.asarray(X, dtype=NP[dtype])
+    Yd = np.asarray(Y, dtype=NP[dtype])
+    A = put(Xd, pa, dev, dtype)
+    B = put(Yd, pb, dev, dtype)
+    C = torch.empty_like(A)
+    unary = op in (4, 5)
+    rc = tl.tl_entrywise(op, tl.Desc(A, n, pa), None if unary else tl.Desc(B, n, pb), alpha,
+                         tl.Desc(C, n, pc))
+    tl.check(rc, "tl_entrywise")
+    torch.cuda.synchronize()
+    got = get(C, n, pc)
+    ref = oracle.entrywise(op, n, synth.to_memory(Xd, pa), oracle.strides(n, pa),
+                           synth.to_memory(Yd, pb), oracle.strides(n, pb), alpha,
+                           wC=oracle.strides(n, pc))
+    return got, synth.from_memory(ref, n, pc).astype(NP[dtype])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("op", sorted(OPS))
+@pytest.mark.parametrize("seed", range(5))
+def test_entrywise_random_layouts_bit_exact(tl, cuda_dev, dtype, op, seed):
+    g = synth.rng(3000 + seed)
+    p = int(g.integers(1, 7))
+    n = tuple(int(x) for x in g.integers(1, 12 if p > 3 else 60, size=p))
+    X = synth.normal(n, 3100 + seed, dtype=np.float64)
+    Y = synth.normal(n, 3200 + seed, dtype=np.float64) + 3.0
+    pa, pb, pc = (synth.random_layout(p, g) for _ in range(3))
+    got, ref = ew_case(tl, cuda_dev, OPS[op], X, Y, pa, pb, pc, dtype)
+    np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("shape", [(1000, 77, 3), (33, 65, 17), (257, 129), (5, 4, 3, 200)])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_entrywise_first_last_mixes_ragged(tl, cuda_dev, shape, dtype):
+    p = len(shape)
+    X = synth.normal(shape, 3300, dtype=np.float64)
+    Y = synth.normal(shape, 3301, dtype=np.float64)
+    F, L = synth.first_order(p), synth.last_order(p)
+    for pa, pb, pc in [(F, L, F), (L, F, F), (F, F, L), (L, L, F), (F, L, L)]:
+        got, ref = ew_case(tl, cuda_dev, 0, X, Y, pa, pb, pc, dtype)
+        np.testing.assert_array_equal(got, ref)
+        got, ref = ew_case(tl, cuda_dev, 4, X, Y, pa, pb, pc, dtype)   # relayout
+        np.testing.assert_array_equal(got, ref)
+
+
+def test_entrywise_small_case_fp64(tl, cuda_dev):
+    case = synth.small_case()
+    got, ref = ew_case(tl, cuda_dev, 0, case.X, case.X, (1, 2, 3), (3, 2, 1), (1, 2, 3), "f64")
+    np.testing.assert_array_equal(got, ref)
+    np.testing.assert_array_equal(got, 2 * case.X)
+
+
+def test_entrywise_strided_and_inplace(tl, cuda_dev):
+    n = (6, 5, 7)
+    npar = (12, 5, 14)
+    parent = synth.normal(npar, 3400, dtype=np.float64)
+    mem = synth.to_memory(parent, (1, 2, 3))
+    w = oracle.strides(npar)
+    nv, wv, gamma = oracle.view(npar, w, (1, 0, 0), (2, 1, 2), (11, 4, 13))
+    assert nv == n
+    Pd = to_dev(mem, cuda_dev, "f64")
+    Y = synth.normal(n, 3401, dtype=np.float64)
+    B = put(Y, (3, 1, 2), cuda_dev, "f64")
+    C = torch.empty(int(np.prod(n)), dtype=torch.float64, device=cuda_dev)
+    Av = tl.Desc(Pd.data_ptr() + gamma * 8, n, w=wv, dtype=torch.float64)
+    tl.check(tl.tl_entrywise(0, Av, tl.Desc(B, n, (3, 1, 2)), 1.0, tl.Desc(C, n)))
+    torch.cuda.synchronize()
+    ref = oracle.entrywise(0, n, mem, wv, synth.to_memory(Y, (3, 1, 2)),
+                           oracle.strides(n, (3, 1, 2)), offA=gamma)
+    np.testing.assert_array_equal(C.cpu().numpy(), ref)
+    # in place: C == A with identical descriptors
+    before = B.clone()
+    tl.check(tl.tl_entrywise(5, tl.Desc(B, n, (3, 1, 2)), None, 2.0, tl.Desc(B, n, (3, 1, 2))))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(B.cpu().numpy(), 2.0 * before.cpu().numpy())
+
+
+def test_entrywise_full_scale_sampled(tl, cuda_dev):
+    case = synth.scale_case()
+    n = case.n
+    memF = case.mem_first
+    X = synth.from_memory(memF, n, synth.first_order(4))
+    memL = synth.to_memory(X, synth.last_order(4))
+    AF, AL = to_dev(memF, cuda_dev, "f32"), to_dev(memL, cuda_dev, "f32")
+    C = torch.empty_like(AF)
+    tl.check(tl.tl_entrywise(0, tl.Desc(AF, n), tl.Desc(AL, n, (4, 3, 2, 1)), 1.0, tl.Desc(C, n)))
+    torch.cuda.synchronize()
+    got = C.cpu().numpy()
+    np.testing.assert_array_equal(got, (memF.astype(np.float64) * 2).astype(np.float32))

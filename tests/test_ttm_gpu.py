@@ -1,0 +1,102 @@
+"""GPU parity of tl_ttm (Sec. 5.2 Eq. 25) against the FP64 oracle.
+
+Bars: integer-valued inputs and identity / permutation matrices are bit-exact;
+otherwise the relative Frobenius error is <= 1e-12 (FP64) and <= 1e-5 (FP32)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import TOL, get, put, rel_err, to_dev, ttm_case
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("seed", range(14))
+def test_ttm_random_layouts(tl, cuda_dev, dtype, seed):
+    g = synth.rng(2000 + seed)
+    p = int(g.integers(2, 7))
+    n = tuple(int(x) for x in g.integers(1, 12 if p > 4 else 40, size=p))
+    q = int(g.integers(1, p + 1))
+    J = int(g.integers(1, 80))
+    X = synth.uniform(n, 2100 + seed)
+    Bm = synth.uniform((J, n[q - 1]), 2200 + seed)
+    acc = bool(g.integers(2))
+    nout = tuple(J if r == q - 1 else x for r, x in enumerate(n))
+    C0 = synth.uniform(nout, 2300 + seed) if acc else None
+    got, ref = ttm_case(tl, cuda_dev, X, q, Bm, synth.random_layout(p, g),
+                        synth.random_layout(p, g), dtype, accumulate=acc, C0=C0,
+                        col_major=bool(g.integers(2)))
+    assert got.shape == ref.shape
+    assert rel_err(got, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_ttm_integer_identity_permutation_exact(tl, cuda_dev, dtype):
+    g = synth.rng(2400)
+    n = (13, 7, 19)
+    X = synth.integers(n, 2401)
+    for q in (1, 2, 3):
+        nq = n[q - 1]
+        for Bm in (np.eye(nq), np.eye(nq)[g.permutation(nq)], synth.integers((5, nq), 2402 + q)):
+            got, ref = ttm_case(tl, cuda_dev, X, q, Bm, synth.random_layout(3, g),
+                                synth.random_layout(3, g), dtype)
+            np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("shape", [(129, 67, 33), (300, 257), (5, 3, 701), (33, 17, 9, 5)])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_ttm_multi_tile_ragged_all_modes(tl, cuda_dev, shape, dtype):
+    X = synth.normal(shape, 2500, dtype=np.float64)
+    p = len(shape)
+    for pi in (synth.first_order(p), synth.last_order(p)):
+        for q in range(1, p + 1):
+            J = 70 if shape[q - 1] > 3 else 3
+            Bm = synth.normal((J, shape[q - 1]), 2501 + q, dtype=np.float64)
+            got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pi, dtype)
+            assert rel_err(got, ref) <= TOL[dtype], (pi, q)
+
+
+def test_ttm_small_case_fp64(tl, cuda_dev):
+    case = synth.small_case()
+    got, ref = ttm_case(tl, cuda_dev, case.X, case.q_ttm, case.B, (1, 2, 3), (1, 2, 3), "f64")
+    assert rel_err(got, ref) <= 1e-12
+
+
+def test_ttm_single_row_matches_ttv(tl, cuda_dev):
+    n = (31, 17, 23)
+    X = synth.normal(n, 2600, dtype=np.float64)
+    for q in (1, 2, 3):
+        b = synth.normal((n[q - 1],), 2601 + q, dtype=np.float64)
+        got, ref = ttm_case(tl, cuda_dev, X, q, b[None, :], (2, 3, 1), (2, 3, 1), "f64")
+        assert rel_err(got, ref) <= 1e-12
+
+
+@pytest.fixture(scope="module")
+def scale_tensors(cuda_dev):
+    case = synth.scale_case()
+    n = case.n
+    memF = case.mem_first
+    X = synth.from_memory(memF, n, synth.first_order(4))
+    memL = synth.to_memory(X, synth.last_order(4))
+    return case, memF, memL, to_dev(memF, cuda_dev, "f32"), to_dev(memL, cuda_dev, "f32")
+
+
+def test_ttm_full_scale_sampled(tl, cuda_dev, scale_tensors):
+    case, memF, memL, AF, AL = scale_tensors
+    n = case.n
+    g = synth.rng(2700)
+    C = torch.empty(128 ** 4, dtype=torch.float32, device=cuda_dev)
+    for pi, mem, Ad in ((synth.first_order(4), memF, AF), (synth.last_order(4), memL, AL)):
+        wA = oracle.strides(n, pi)
+        for q in range(1, 5):
+            Bm = case.matrices[q - 1]
+            Bt = to_dev(Bm.reshape(-1), cuda_dev, "f32")
+            tl.check(tl.tl_ttm(tl.Desc(Ad, n, pi), Bt, 128, 128, 1, q, tl.Desc(C, n, pi)))
+            torch.cuda.synchronize()
+            got = get(C, n, pi)
+            idx = np.stack([g.integers(0, x, size=3000) for x in n], axis=1)
+            ref = oracle.ttm_at(mem, n, wA, q, Bm.reshape(-1), 128, 1, idx)
+            assert rel_err(got[tuple(idx.T)], ref) <= 1e-5, (pi, q)
