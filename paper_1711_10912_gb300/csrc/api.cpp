@@ -20,16 +20,18 @@ namespace tl {
 
 int device_sms()
 {
-    static std::mutex mu;
-    static std::map<int, int> cache;
+    // per-device cache in a fixed table: the query path allocates nothing
+    constexpr int kMaxDevices = 64;
+    static std::atomic<int> cache[kMaxDevices];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(dev);
-    if (it != cache.end()) return it->second;
+    if (dev >= 0 && dev < kMaxDevices) {
+        int v = cache[dev].load(std::memory_order_relaxed);
+        if (v > 0) return v;
+    }
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    cache[dev] = sms;
+    if (dev >= 0 && dev < kMaxDevices) cache[dev].store(sms, std::memory_order_relaxed);
     return sms;
 }
 

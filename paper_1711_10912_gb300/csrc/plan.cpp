@@ -1,6 +1,6 @@
 // plan.cpp -- descriptor validation, stride derivation (Sec. 3.1 Eq. 14) and
 // joint mode collapsing for ttv, ttm and entrywise calls.  Host only; no
-// CUDA calls, no allocation.
+// CUDA calls, no heap allocation, O(p^2) work.
 #include "plan.h"
 
 #include <algorithm>
@@ -38,7 +38,14 @@ static bool no_self_overlap(const Tensor& t)
     int m = 0;
     for (uint32_t r = 0; r < t.p; ++r)
         if (t.n[r] > 1) idx[m++] = (int)r;
-    std::sort(idx, idx + m, [&](int a, int b) { return t.w[a] < t.w[b]; });
+    for (int i = 1; i < m; ++i) {
+        int x = idx[i], j = i - 1;
+        while (j >= 0 && t.w[x] < t.w[idx[j]]) {
+            idx[j + 1] = idx[j];
+            --j;
+        }
+        idx[j + 1] = x;
+    }
     int64_t reach = 0;
     for (int i = 0; i < m; ++i) {
         if (t.w[idx[i]] <= reach) return false;
@@ -79,12 +86,22 @@ void collapse(Space& sp, int key)
         if (sp.d[i].n > 1) sp.d[m++] = sp.d[i];
     sp.nd = m;
     // 2. sort by the key operand's stride, ties by the other operands
-    std::stable_sort(sp.d, sp.d + sp.nd, [&](const Dim& a, const Dim& b) {
+    //    (insertion sort: stable, at most kMaxDims entries, no allocation)
+    auto less = [&](const Dim& a, const Dim& b) {
         if (a.s[key] != b.s[key]) return a.s[key] < b.s[key];
         for (int o = 0; o < sp.nops; ++o)
             if (a.s[o] != b.s[o]) return a.s[o] < b.s[o];
         return false;
-    });
+    };
+    for (int i = 1; i < sp.nd; ++i) {
+        Dim x = sp.d[i];
+        int j = i - 1;
+        while (j >= 0 && less(x, sp.d[j])) {
+            sp.d[j + 1] = sp.d[j];
+            --j;
+        }
+        sp.d[j + 1] = x;
+    }
     // 3. merge neighbours that are adjacent in memory for every operand
     if (sp.nd == 0) return;
     int out = 0;
