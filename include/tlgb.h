@@ -108,6 +108,33 @@ int tl_ttv(const tl_tensor* A, const void* b, int64_t incb, uint32_t q,
            const tl_tensor* C, int32_t accumulate, void* stream);
 
 /*
+ * tl_ttv_noalloc -- tl_ttv that allocates no device memory.  The paper has
+ * no counterpart; this entry point is for callers that cannot let a library
+ * call cudaMalloc: runtimes that own every byte of device memory through
+ * their own allocator and budget (an allocation behind their back can fail
+ * or break the budget), and latency-critical loops in which a cudaMalloc /
+ * cudaFree, which can synchronise the device, is not acceptable.
+ * Arguments, results and errors are those of tl_ttv, with these differences:
+ *  - Scratch: when the planner splits the contraction across CTAs, the
+ *    partial sums go to one static device array of
+ *    TL_TTV_NOALLOC_SCRATCH_BYTES (4 MiB) that belongs to the library image:
+ *    every GPU that loads the library holds it until the process exits.  A
+ *    call whose partial sums would need more returns TL_ENOMEM and enqueues
+ *    nothing; tl_ttv (which grows a workspace) handles such calls.
+ *  - The first call on a device looks the array's device address up (once
+ *    per device, with that device current); make that first call before any
+ *    stream capture.
+ *  - All calls on a device share the array, which keeps the last call's
+ *    contents.  Every partial sum is written before it is read, so nothing
+ *    needs clearing; but calls whose kernels overlap on the GPU (for example
+ *    on two streams without an event between them) race on the array and
+ *    must be serialised by the caller.
+ */
+#define TL_TTV_NOALLOC_SCRATCH_BYTES (4u << 20)
+int tl_ttv_noalloc(const tl_tensor* A, const void* b, int64_t incb, uint32_t q,
+                   const tl_tensor* C, int32_t accumulate, void* stream);
+
+/*
  * tl_ttm -- mode-q tensor-times-matrix, Sec. 5.2 Eq. 25:
  *   C(i_1..j..i_p) = sum_{k=0}^{n_q-1} A(i_1..k..i_p) * B(j, k),  0 <= j < J
  * B: device J x n_q matrix of A's dtype, B(j,k) at B[j*ldb_row + k*ldb_col]

@@ -145,6 +145,8 @@ def load_library():
 def _declare(_lib):
     _lib.tl_ttv.argtypes = [_T, ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, _T,
                             ctypes.c_int32, ctypes.c_void_p]
+    _lib.tl_ttv_noalloc.argtypes = [_T, ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, _T,
+                                     ctypes.c_int32, ctypes.c_void_p]
     _lib.tl_ttm.argtypes = [_T, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                             ctypes.c_uint32, _T, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
     _lib.tl_entrywise.argtypes = [ctypes.c_int32, _T, _T, ctypes.c_double, _T, ctypes.c_void_p]
@@ -187,6 +189,15 @@ def tl_strerror(code: int) -> str:
 
 def tl_ttv(A: Desc, b, incb: int, q: int, C: Desc, accumulate: int = 0, stream=None) -> int:
     return _lib.tl_ttv(A.ref, _addr(b), int(incb), int(q), C.ref, int(accumulate), _stream(stream))
+
+
+def tl_ttv_noalloc(A: Desc, b, incb: int, q: int, C: Desc, accumulate: int = 0,
+                   stream=None) -> int:
+    return _lib.tl_ttv_noalloc(A.ref, _addr(b), int(incb), int(q), C.ref, int(accumulate),
+                               _stream(stream))
+
+
+TL_TTV_NOALLOC_SCRATCH_BYTES = 4 << 20
 
 
 def tl_ttm(A: Desc, B, J: int, ldb_row: int, ldb_col: int, q: int, C: Desc,

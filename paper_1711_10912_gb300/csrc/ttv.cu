@@ -268,3 +268,73 @@ int launch_ttv(const TtvPlan& P, const void* A, const void* b, void* C, void* ws
 }
 
 }  // namespace tl
+
+// ------------------------------------------------------------------------
+// tl_ttv_noalloc: the same kernels with the split-K partial sums in a static
+// device array instead of the library's per-stream workspace, so the call
+// allocates no device memory (see tlgb.h for who needs this).
+// ------------------------------------------------------------------------
+
+#include <atomic>
+#include <mutex>
+
+#include "runtime.h"
+
+static __device__ __align__(256) unsigned char g_ttv_noalloc_scratch[TL_TTV_NOALLOC_SCRATCH_BYTES];
+
+namespace tl {
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::atomic<void*> g_scratch_addr[kMaxDevices];
+std::mutex g_scratch_mu;
+
+// Device address of g_ttv_noalloc_scratch on the current device.  In host
+// code the symbol names a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+int noalloc_scratch(void** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TL_ECUDA;
+    void* p = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        p = g_scratch_addr[dev].load(std::memory_order_relaxed);
+        if (!p) {
+            cudaError_t e = cudaGetSymbolAddress(&p, g_ttv_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                return TL_ECUDA;
+            }
+            g_scratch_addr[dev].store(p, std::memory_order_release);
+        }
+    }
+    *out = p;
+    return TL_OK;
+}
+
+}  // namespace
+}  // namespace tl
+
+extern "C" int tl_ttv_noalloc(const tl_tensor* A_, const void* b, int64_t incb, uint32_t q,
+                              const tl_tensor* C_, int32_t accumulate, void* stream)
+{
+    using namespace tl;
+    Tensor A, C;
+    TtvPlan P;
+    int sms = device_sms();
+    if (sms <= 0) return TL_ECUDA;
+    int rc = prepare_ttv(A_, b, incb, q, C_, sms, A, C, P);
+    if (rc) return rc;
+    size_t need = ttv_workspace_bytes(P);
+    if (need > (size_t)TL_TTV_NOALLOC_SCRATCH_BYTES) return TL_ENOMEM;
+    void* ws = nullptr;
+    if (need) {
+        rc = noalloc_scratch(&ws);
+        if (rc) return rc;
+    }
+    rc = launch_ttv(P, A.data, b, C.data, ws, accumulate ? 1 : 0, sms,
+                    static_cast<cudaStream_t>(stream));
+    if (rc == TL_OK) count_launches(P.splits > 1 ? 2 : 1);
+    return rc;
+}
