@@ -54,7 +54,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tlgb", choices=["tlgb", "reference"])
     ap.add_argument("--edge", type=int, default=128, help="extent of every mode (workload size)")
-    ap.add_argument("--ttm-precision", type=int, default=2,
+    ap.add_argument("--ttm-precision", type=int, default=5,
                     help="TL_P_* for the ttm calls (2 = FP32 SIMT, 5 = split-BF16x3)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -188,6 +188,16 @@ int tl_version(void);
 uint64_t tl_launch_count(void);
 
 /*
+ * tl_device_status -- synchronises `stream`, then reports whether any
+ * bounded device-side wait of the library's pipelined kernels gave up since
+ * the last call: TL_ETIMEOUT (and the flag is cleared) or TL_OK.  Such a
+ * kernel does not hang: after about two seconds without progress it records
+ * the timeout, drains its own copies, frees its tensor memory and returns,
+ * leaving its output incomplete.
+ */
+int tl_device_status(void* stream);
+
+/*
  * tl_plan_describe -- host-only: validates the arguments of a ttv (op 0),
  * ttm (op 1) or entrywise (op 2) call exactly as the entry point would and
  * writes a one-line JSON description of the collapsed iteration space and

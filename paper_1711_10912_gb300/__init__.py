@@ -153,6 +153,7 @@ def _declare(_lib):
     _lib.tl_norm.argtypes = [_T, ctypes.c_void_p, ctypes.c_void_p]
     _lib.tl_rel_error.argtypes = [_T, _T, ctypes.c_void_p, ctypes.c_void_p]
     _lib.tl_launch_count.restype = ctypes.c_uint64
+    _lib.tl_device_status.argtypes = [ctypes.c_void_p]
     _lib.tl_strerror.argtypes = [ctypes.c_int]
     _lib.tl_strerror.restype = ctypes.c_char_p
     _lib.tl_plan_describe.argtypes = [ctypes.c_int32, _T, _T, ctypes.c_uint32, ctypes.c_int64,
@@ -181,6 +182,10 @@ def tl_version() -> int:
 
 def tl_launch_count() -> int:
     return int(_lib.tl_launch_count())
+
+
+def tl_device_status(stream=None) -> int:
+    return _lib.tl_device_status(_stream(stream))
 
 
 def tl_strerror(code: int) -> str:

@@ -183,6 +183,12 @@ int tl_version(void) { return 100; }
 
 uint64_t tl_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int tl_device_status(void* stream)
+{
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return TL_ECUDA;
+    return ttm_tc_status(true);
+}
+
 const char* tl_strerror(int code)
 {
     switch (code) {

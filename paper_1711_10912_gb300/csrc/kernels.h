@@ -33,4 +33,7 @@ int launch_ttm_tc(const TtmPlan& P, const void* A, const void* B, void* C, int a
                   int num_sms, cudaStream_t st);
 // kernels one launch_ttm_tc call enqueues
 int ttm_tc_launches(const TtmPlan& P);
+// TL_ETIMEOUT if a bounded wait in a tensor-core kernel gave up since the
+// last cleared check, else TL_OK (reads the device status word).
+int ttm_tc_status(bool clear);
 }  // namespace tl

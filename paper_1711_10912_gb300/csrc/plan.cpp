@@ -233,6 +233,22 @@ int plan_ttm(const Tensor& A, int64_t J, int64_t ldb_row, int64_t ldb_col, uint3
     P.M = P.rows.count();
     P.kernel = K_TTM_SIMT;
     P.tc_variant = 0;
+    // Tensor-core path: FP32 data in a tensor-core precision, a contraction
+    // and output width worth an MMA, and an A that a TMA box can describe
+    // (16-byte aligned base and strides).
+    const bool tc_prec = precision == TL_P_TF32 || precision == TL_P_BF16 ||
+                         precision == TL_P_BF16X3;
+    if (tc_prec && A.dtype == TL_F32 && J <= 512 && P.nq >= 16 && aligned(A.data, 16)) {
+        if (P.saq == 1 && P.rows.nd == 1 && P.M >= 128 && P.rows.d[0].s[0] % 4 == 0) {
+            P.kernel = K_TTM_TC;
+            P.tc_variant = 1;   // rows contiguous in k
+        } else if (P.saq > 1 && P.saq % 4 == 0 && P.rows.nd >= 1 && P.rows.nd <= 2 &&
+                   P.rows.d[0].s[0] == 1 && P.rows.d[0].n >= 64 &&
+                   (P.rows.nd == 1 || P.rows.d[1].s[0] % 4 == 0)) {
+            P.kernel = K_TTM_TC;
+            P.tc_variant = 2;   // rows contiguous in the fastest output mode
+        }
+    }
     return TL_OK;
 }
 

@@ -1,15 +1,748 @@
-// ttm_tc.cu -- tcgen05 tensor-core ttm (placeholder until the kernel lands).
+// ttm_tc.cu -- mode-q tensor-times-matrix on the tcgen05 tensor cores,
+// Sec. 5.2 Eq. 25:  C(i with i_q = j) = sum_k A(i with i_q = k) * B(j, k).
+//
+// The rows of the product are the non-contracted elements of A (m), the
+// columns are j and the reduction runs over k = i_q, i.e. the paper's
+// slice-times-matrix reading of ttm with every slice batched into one GEMM.
+// Two row orientations are supported (chosen by the planner):
+//   ROW  w_q = 1: row m of A is contiguous in k (A is M x n_q, row stride
+//        lda), loaded by a 2-D TMA box of 128 rows x 32 k (128-byte swizzle);
+//   COL  the fastest output mode i has unit stride in A and w_q > 1: the
+//        rows of one tile are 128 consecutive i of one outer index o, loaded
+//        by a 3-D TMA box of 128 i x 32 k x 1 o.
+// FP32 data is converted on chip: four converter warps read the FP32 tile,
+// round it to TF32, to BF16, or split it into BF16 hi + lo (hi = RN(a),
+// lo = RN(a - hi)), and write the tensor-core operand in the K-major,
+// no-swizzle canonical layout (8-row x 16-byte core matrices).  B is
+// converted once per call into the same layout in global scratch and
+// streamed per k stage with bulk copies.  Split-BF16x3 issues
+// hi*hi + hi*lo + lo*hi; every product accumulates in FP32 in TMEM.
+//
+// Warp roles (320 threads, one CTA per SM, persistent over tiles):
+//   warp 0      TMA producer (one thread)
+//   warp 1      TMEM allocator and MMA issuer (one thread)
+//   warps 2-5   converters
+//   warps 6-9   epilogue: TMEM -> registers -> C (each warp owns the TMEM
+//               lane quarter warp % 4)
+// Every mbarrier wait is bounded: after about a second without progress the
+// thread records a timeout in a status word, the CTA drains its TMA copies,
+// frees its TMEM and returns, and tl_device_status() reports TL_ETIMEOUT.
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <atomic>
+#include <cstdint>
+#include <mutex>
 
 #include "kernels.h"
+#include "runtime.h"
 
 namespace tl {
 
-int launch_ttm_tc(const TtmPlan&, const void*, const void*, void*, int, int, cudaStream_t)
+__device__ unsigned int g_tc_status;
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 32;                 // k per stage
+constexpr int kThreads = 320;
+constexpr int kTmemCols = 512;
+constexpr long long kTimeoutCycles = 4000000000LL;   // about 2 s at 2 GHz
+
+enum Variant { V_NONE = 0, V_ROW = 1, V_COL = 2 };
+
+// ------------------------------------------------------------ PTX helpers --
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
-    return TL_EUNSUPPORTED;
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-int ttm_tc_launches(const TtmPlan&) { return 0; }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false (and the status word set) after kTimeoutCycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    if (mbar_try(bar, parity)) return true;
+    long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (clock64() - t0 > kTimeoutCycles) {
+            atomicOr(&g_tc_status, 1u);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// UMMA shared-memory descriptor, K-major, no swizzle: 8-row x 16-byte core
+// matrices; lbo = byte distance between core matrices along K, sbo = byte
+// distance between 8-row groups.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;            // descriptor version for tcgen05
+    return d;                          // base offset 0, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor: D = F32, A/B format (1 = BF16, 2 = TF32), both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc(uint32_t fmt, uint32_t M, uint32_t N)
+{
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void umma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                     uint32_t accum)
+{
+    if constexpr (TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+    }
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// ------------------------------------------------------------ parameters --
+
+struct TcArgs {
+    float* C;
+    const uint8_t* bimg;     // converted B, [ks][part][Jp x BK] canonical tiles
+    int variant;
+    int prec;                // TL_P_TF32, TL_P_BF16, TL_P_BF16X3
+    int nparts;              // 1 or 2 (hi, lo)
+    int esize;               // operand element bytes (4 tf32, 2 bf16)
+    int J, Jp, nks;
+    int ns_stg, ns_op;
+    int nacc;                // TMEM accumulator buffers (2 when Jp <= 256)
+    int accumulate;
+    int64_t ntiles;
+    int64_t M;               // ROW: rows; COL: inner extent
+    int64_t tiles_per_o;     // COL
+    int64_t sc_m;            // ROW: C stride of m; COL: C stride of i
+    int64_t sc_o;            // COL: C stride of o
+    int64_t scq;             // C stride of j
+    uint32_t a_stage_bytes;  // FP32 staging tile
+    uint32_t opa_part_bytes, opb_part_bytes;
+    uint32_t off_stg, off_op, op_stage_bytes, off_bar;
+};
+
+struct Bars {
+    uint32_t stg_full, stg_empty, op_full, op_empty, acc_full, acc_empty, tmem_slot;
+};
+
+__device__ __forceinline__ Bars bar_layout(uint32_t base, const TcArgs& a)
+{
+    Bars b;
+    b.stg_full = base;
+    b.stg_empty = b.stg_full + 8 * a.ns_stg;
+    b.op_full = b.stg_empty + 8 * a.ns_stg;
+    b.op_empty = b.op_full + 8 * a.ns_op;
+    b.acc_full = b.op_empty + 8 * a.ns_op;
+    b.acc_empty = b.acc_full + 16;
+    b.tmem_slot = b.acc_empty + 16;
+    return b;
+}
+
+// Pipeline position: stage index and the parity of its current phase.
+struct Pipe {
+    int idx = 0;
+    uint32_t phase = 0;
+    __device__ void next(int n)
+    {
+        if (++idx == n) { idx = 0; phase ^= 1u; }
+    }
+};
+
+// ---------------------------------------------------------------- kernel --
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1)
+ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // align the dynamic shared memory base to 1024 bytes (128-byte swizzle atoms)
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* sbase = smem_raw + (base - raw);
+    const Bars bars = bar_layout(base + a.off_bar, a);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr bool kTF32 = (PREC == TL_P_TF32);
+    constexpr int kParts = (PREC == TL_P_BF16X3) ? 2 : 1;
+    constexpr int kKmma = kTF32 ? 8 : 16;           // k per MMA instruction
+    constexpr int kSubs = BK / kKmma;
+    constexpr int kChunks = BK * (kTF32 ? 4 : 2) / 16;   // 16-byte chunks per operand row
+    constexpr uint32_t kSbo = kChunks * 128;        // bytes per 8-row group
+    constexpr uint32_t kLbo = 128;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.ns_stg; ++s) {
+            mbar_init(bars.stg_full + 8 * s, 1);
+            mbar_init(bars.stg_empty + 8 * s, 128);
+        }
+        for (int s = 0; s < a.ns_op; ++s) {
+            mbar_init(bars.op_full + 8 * s, 1 + 128);
+            mbar_init(bars.op_empty + 8 * s, 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(bars.acc_full + 8 * s, 1);
+            mbar_init(bars.acc_empty + 8 * s, 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(bars.tmem_slot), "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t*>(sbase + (bars.tmem_slot - base));
+    const uint32_t acc_cols = a.nacc == 2 ? 256u : 512u;
+
+    auto op_a = [&](int stage, int part) -> uint32_t {
+        return base + a.off_op + stage * a.op_stage_bytes + part * a.opa_part_bytes;
+    };
+    auto op_b = [&](int stage, int part) -> uint32_t {
+        return base + a.off_op + stage * a.op_stage_bytes + kParts * a.opa_part_bytes +
+               part * a.opb_part_bytes;
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------------ producer
+        if (lane == 0) {
+            Pipe st, op;
+            bool ok = true;
+            // parity of the last arm of each stage, to drain on exit
+            uint32_t stg_armed = 0, stg_par = 0, op_armed = 0, op_par = 0;
+            for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+                int64_t o = 0, r0;
+                if (a.variant == V_COL) {
+                    o = tile / a.tiles_per_o;
+                    r0 = (tile % a.tiles_per_o) * BM;
+                } else {
+                    r0 = tile * BM;
+                }
+                for (int ks = 0; ks < a.nks && ok; ++ks) {
+                    if (!(ok = mbar_wait(bars.stg_empty + 8 * st.idx, st.phase ^ 1u))) break;
+                    uint32_t sb = bars.stg_full + 8 * st.idx;
+                    mbar_arrive_tx(sb, a.a_stage_bytes);
+                    uint32_t dst = base + a.off_stg + st.idx * a.a_stage_bytes;
+                    if (a.variant == V_COL)
+                        tma_load_3d(dst, &tmap, (int)r0, ks * BK, (int)o, sb);
+                    else
+                        tma_load_2d(dst, &tmap, ks * BK, (int)r0, sb);
+                    stg_armed |= 1u << st.idx;
+                    stg_par = (stg_par & ~(1u << st.idx)) | (st.phase << st.idx);
+                    st.next(a.ns_stg);
+
+                    if (!(ok = mbar_wait(bars.op_empty + 8 * op.idx, op.phase ^ 1u))) break;
+                    uint32_t ob = bars.op_full + 8 * op.idx;
+                    mbar_arrive_tx(ob, kParts * a.opb_part_bytes);
+                    for (int part = 0; part < kParts; ++part)
+                        bulk_load(op_b(op.idx, part),
+                                  a.bimg + ((size_t)ks * kParts + part) * a.opb_part_bytes,
+                                  a.opb_part_bytes, ob);
+                    op_armed |= 1u << op.idx;
+                    op_par = (op_par & ~(1u << op.idx)) | (op.phase << op.idx);
+                    op.next(a.ns_op);
+                }
+            }
+            if (!ok) {
+                // drain: every copy issued must land before the CTA exits
+                for (int s = 0; s < a.ns_stg; ++s)
+                    if (stg_armed & (1u << s)) {
+                        long long t0 = clock64();
+                        while (!mbar_try(bars.stg_full + 8 * s, (stg_par >> s) & 1u) &&
+                               clock64() - t0 < kTimeoutCycles) {}
+                    }
+                for (int s = 0; s < a.ns_op; ++s)
+                    if (op_armed & (1u << s)) {
+                        long long t0 = clock64();
+                        while (!mbar_try(bars.op_full + 8 * s, (op_par >> s) & 1u) &&
+                               clock64() - t0 < kTimeoutCycles) {}
+                    }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            Pipe op, acc;
+            bool ok = true;
+            const int nchunks = (a.Jp + 255) / 256;
+            for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+                if (!(ok = mbar_wait(bars.acc_empty + 8 * acc.idx, acc.phase ^ 1u))) break;
+                tc_fence_after();
+                const uint32_t dcol = tmem_base + acc.idx * acc_cols;
+                for (int ks = 0; ks < a.nks && ok; ++ks) {
+                    if (!(ok = mbar_wait(bars.op_full + 8 * op.idx, op.phase))) break;
+                    tc_fence_after();
+#pragma unroll
+                    for (int sub = 0; sub < kSubs; ++sub) {
+                        for (int c = 0; c < nchunks; ++c) {
+                            const uint32_t n = (c == nchunks - 1) ? (uint32_t)(a.Jp - 256 * c) : 256u;
+                            const uint32_t idesc = umma_idesc(kTF32 ? 2u : 1u, BM, n);
+                            const uint32_t boff = (uint32_t)c * (256u / 8u) * kSbo + sub * 2 * kLbo;
+                            const uint32_t aoff = sub * 2 * kLbo;
+                            const uint32_t d = dcol + 256u * c;
+                            uint32_t accum = (ks > 0 || sub > 0) ? 1u : 0u;
+                            umma<kTF32>(d, umma_desc(op_a(op.idx, 0) + aoff, kLbo, kSbo),
+                                        umma_desc(op_b(op.idx, 0) + boff, kLbo, kSbo), idesc, accum);
+                            if constexpr (kParts == 2) {
+                                umma<kTF32>(d, umma_desc(op_a(op.idx, 0) + aoff, kLbo, kSbo),
+                                            umma_desc(op_b(op.idx, 1) + boff, kLbo, kSbo), idesc, 1u);
+                                umma<kTF32>(d, umma_desc(op_a(op.idx, 1) + aoff, kLbo, kSbo),
+                                            umma_desc(op_b(op.idx, 0) + boff, kLbo, kSbo), idesc, 1u);
+                            }
+                        }
+                    }
+                    umma_commit(bars.op_empty + 8 * op.idx);
+                    op.next(a.ns_op);
+                }
+                if (!ok) break;
+                umma_commit(bars.acc_full + 8 * acc.idx);
+                acc.next(a.nacc);
+            }
+        }
+    } else if (warp < 6) {
+        // ------------------------------------------------------ converters
+        const int t = threadIdx.x - 64;          // operand row 0..127
+        Pipe st, op;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+            for (int ks = 0; ks < a.nks && ok; ++ks) {
+                if (!(ok = mbar_wait(bars.stg_full + 8 * st.idx, st.phase))) break;
+                if (!(ok = mbar_wait(bars.op_empty + 8 * op.idx, op.phase ^ 1u))) break;
+                const float* stg = reinterpret_cast<const float*>(
+                    sbase + a.off_stg + st.idx * a.a_stage_bytes);
+                float x[BK];
+                if (a.variant == V_COL) {
+                    // staging is [BK k][128 i]: column t
+#pragma unroll
+                    for (int k = 0; k < BK; ++k) x[k] = stg[k * BM + t];
+                } else {
+                    // staging is [128 m][BK k] with 128-byte swizzle
+                    const float4* row = reinterpret_cast<const float4*>(stg + t * BK);
+#pragma unroll
+                    for (int c = 0; c < BK / 4; ++c) {
+                        float4 v = row[c ^ (t & 7)];
+                        x[4 * c] = v.x;
+                        x[4 * c + 1] = v.y;
+                        x[4 * c + 2] = v.z;
+                        x[4 * c + 3] = v.w;
+                    }
+                }
+                const uint32_t row_off = (uint32_t)(t >> 3) * kSbo + (uint32_t)(t & 7) * 16u;
+                uint8_t* pa0 = sbase + (op_a(op.idx, 0) - base) + row_off;
+                if constexpr (kTF32) {
+#pragma unroll
+                    for (int c = 0; c < kChunks; ++c) {
+                        uint4 v = make_uint4(to_tf32(x[4 * c]), to_tf32(x[4 * c + 1]),
+                                             to_tf32(x[4 * c + 2]), to_tf32(x[4 * c + 3]));
+                        *reinterpret_cast<uint4*>(pa0 + c * 128) = v;
+                    }
+                } else {
+                    uint8_t* pa1 = sbase + (op_a(op.idx, kParts - 1) - base) + row_off;
+#pragma unroll
+                    for (int c = 0; c < kChunks; ++c) {
+                        float h[8], l[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            h[e] = __bfloat162float(__float2bfloat16_rn(x[8 * c + e]));
+                            l[e] = x[8 * c + e] - h[e];
+                        }
+                        uint4 vh = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]),
+                                              pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
+                        *reinterpret_cast<uint4*>(pa0 + c * 128) = vh;
+                        if constexpr (kParts == 2) {
+                            uint4 vl = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]),
+                                                  pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
+                            *reinterpret_cast<uint4*>(pa1 + c * 128) = vl;
+                        }
+                    }
+                }
+                fence_proxy_async();
+                mbar_arrive(bars.stg_empty + 8 * st.idx);
+                mbar_arrive(bars.op_full + 8 * op.idx);
+                st.next(a.ns_stg);
+                op.next(a.ns_op);
+            }
+        }
+    } else {
+        // ------------------------------------------------------ epilogue
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        Pipe acc;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+            if (!(ok = mbar_wait(bars.acc_full + 8 * acc.idx, acc.phase))) break;
+            tc_fence_after();
+            bool valid;
+            int64_t offc;
+            if (a.variant == V_COL) {
+                int64_t o = tile / a.tiles_per_o;
+                int64_t i = (tile % a.tiles_per_o) * BM + row;
+                valid = i < a.M;
+                offc = o * a.sc_o + i * a.sc_m;
+            } else {
+                int64_t m = tile * BM + row;
+                valid = m < a.M;
+                offc = m * a.sc_m;
+            }
+            const uint32_t tcol = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc.idx * acc_cols;
+            for (int c0 = 0; c0 < a.Jp; c0 += 32) {
+                float v[32];
+                tmem_ld32(tcol + c0, v);
+                if (valid) {
+                    float* pc = a.C + offc;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        int jg = c0 + j;
+                        if (jg < a.J) {
+                            float* p = pc + (int64_t)jg * a.scq;
+                            *p = a.accumulate ? *p + v[j] : v[j];
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(bars.acc_empty + 8 * acc.idx);
+            acc.next(a.nacc);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(kTmemCols));
+    }
+}
+
+// B(j, k) -> canonical K-major tiles [ks][part][Jp rows x BK], 16 bytes per thread.
+template <int PREC>
+__global__ void ttm_tc_prep_b(const float* __restrict__ B, int64_t ldb_row, int64_t ldb_col, int J,
+                              int Jp, int64_t nq, int nks, uint8_t* __restrict__ img,
+                              uint32_t part_bytes)
+{
+    constexpr bool kTF32 = (PREC == TL_P_TF32);
+    constexpr int kParts = (PREC == TL_P_BF16X3) ? 2 : 1;
+    constexpr int kEl = kTF32 ? 4 : 8;                  // elements per 16-byte chunk
+    constexpr int kChunks = BK / kEl;
+    constexpr uint32_t kSbo = kChunks * 128;
+    const int64_t total = (int64_t)nks * Jp * kChunks;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t % kChunks);
+        const int j = (int)((t / kChunks) % Jp);
+        const int ks = (int)(t / ((int64_t)kChunks * Jp));
+        float x[kEl];
+#pragma unroll
+        for (int e = 0; e < kEl; ++e) {
+            int64_t k = (int64_t)ks * BK + c * kEl + e;
+            x[e] = (j < J && k < nq) ? B[j * ldb_row + k * ldb_col] : 0.f;
+        }
+        const uint32_t off = (uint32_t)(j >> 3) * kSbo + (uint32_t)c * 128u + (uint32_t)(j & 7) * 16u;
+        uint8_t* p0 = img + ((size_t)ks * kParts) * part_bytes + off;
+        if constexpr (kTF32) {
+            *reinterpret_cast<uint4*>(p0) =
+                make_uint4(to_tf32(x[0]), to_tf32(x[1]), to_tf32(x[2]), to_tf32(x[3]));
+        } else {
+            float h[8], l[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                h[e] = __bfloat162float(__float2bfloat16_rn(x[e]));
+                l[e] = x[e] - h[e];
+            }
+            *reinterpret_cast<uint4*>(p0) = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]),
+                                                       pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
+            if constexpr (kParts == 2) {
+                uint8_t* p1 = p0 + part_bytes;
+                *reinterpret_cast<uint4*>(p1) =
+                    make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]),
+                               pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------- host side --
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static std::atomic<void*> fn{nullptr};
+    void* p = fn.load();
+    if (!p) {
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        fn.store(p);
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+}
+
+struct Layout {
+    int nparts, esize, Jp, nks, ns_stg, ns_op, nacc;
+    uint32_t a_stage, opa_part, opb_part, op_stage, off_stg, off_op, off_bar, smem;
+};
+
+Layout layout_for(const TtmPlan& P)
+{
+    Layout L{};
+    L.nparts = P.precision == TL_P_BF16X3 ? 2 : 1;
+    L.esize = P.precision == TL_P_TF32 ? 4 : 2;
+    L.Jp = (int)((P.J + 15) / 16 * 16);
+    L.nks = (int)((P.nq + BK - 1) / BK);
+    L.nacc = L.Jp <= 256 ? 2 : 1;
+    L.a_stage = BM * BK * 4;
+    L.opa_part = BM * BK * L.esize;
+    L.opb_part = (uint32_t)L.Jp * BK * L.esize;
+    L.op_stage = L.nparts * (L.opa_part + L.opb_part);
+    const uint32_t budget = 227 * 1024 - 1024 - 256;    // alignment slack + barriers
+    L.ns_stg = 4;
+    L.ns_op = 4;
+    while (L.ns_op > 2 && L.ns_stg * L.a_stage + L.ns_op * L.op_stage > budget) --L.ns_op;
+    while (L.ns_stg > 2 && L.ns_stg * L.a_stage + L.ns_op * L.op_stage > budget) --L.ns_stg;
+    L.off_stg = 0;
+    L.off_op = L.ns_stg * L.a_stage;
+    L.off_bar = L.off_op + L.ns_op * L.op_stage;
+    L.smem = L.off_bar + 8 * (2 * L.ns_stg + 2 * L.ns_op + 4) + 16 + 1024;
+    // more than half of the SM's shared memory keeps one CTA per SM, so no
+    // two CTAs ever wait on each other for the 512 TMEM columns
+    if (L.smem < 116 * 1024) L.smem = 116 * 1024;
+    return L;
+}
+
+template <int PREC>
+int launch_prec(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate, int sms,
+                cudaStream_t st)
+{
+    const Layout L = layout_for(P);
+    if (L.smem > 227 * 1024) return TL_EUNSUPPORTED;
+    auto enc = encode_fn();
+    if (!enc) return TL_ECUDA;
+
+    TcArgs a{};
+    a.C = static_cast<float*>(C);
+    a.variant = P.tc_variant;
+    a.prec = PREC;
+    a.nparts = L.nparts;
+    a.esize = L.esize;
+    a.J = (int)P.J;
+    a.Jp = L.Jp;
+    a.nks = L.nks;
+    a.ns_stg = L.ns_stg;
+    a.ns_op = L.ns_op;
+    a.nacc = L.nacc;
+    a.accumulate = accumulate;
+    a.scq = P.scq;
+    a.a_stage_bytes = L.a_stage;
+    a.opa_part_bytes = L.opa_part;
+    a.opb_part_bytes = L.opb_part;
+    a.off_stg = L.off_stg;
+    a.off_op = L.off_op;
+    a.op_stage_bytes = L.op_stage;
+    a.off_bar = L.off_bar;
+
+    CUtensorMap map;
+    CUresult cr;
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (P.tc_variant == V_ROW) {
+        const int64_t lda = P.rows.nd ? P.rows.d[0].s[0] : P.nq;
+        a.M = P.M;
+        a.ntiles = (P.M + BM - 1) / BM;
+        a.sc_m = P.rows.nd ? P.rows.d[0].s[1] : 0;
+        const cuuint64_t gdim[2] = {(cuuint64_t)P.nq, (cuuint64_t)P.M};
+        const cuuint64_t gstr[1] = {(cuuint64_t)lda * 4};
+        const cuuint32_t box[2] = {BK, BM};
+        cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(A), gdim, gstr, box,
+                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const int64_t inner = P.rows.d[0].n;
+        const int64_t outer = P.rows.nd == 2 ? P.rows.d[1].n : 1;
+        const int64_t sa_o = P.rows.nd == 2 ? P.rows.d[1].s[0] : inner * P.nq;
+        a.M = inner;
+        a.tiles_per_o = (inner + BM - 1) / BM;
+        a.ntiles = a.tiles_per_o * outer;
+        a.sc_m = P.rows.d[0].s[1];
+        a.sc_o = P.rows.nd == 2 ? P.rows.d[1].s[1] : 0;
+        const cuuint64_t gdim[3] = {(cuuint64_t)inner, (cuuint64_t)P.nq, (cuuint64_t)outer};
+        const cuuint64_t gstr[2] = {(cuuint64_t)P.saq * 4, (cuuint64_t)sa_o * 4};
+        const cuuint32_t box[3] = {BM, BK, 1};
+        cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(A), gdim, gstr, box,
+                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (cr != CUDA_SUCCESS) return TL_EUNSUPPORTED;
+
+    // converted B in the per-stream workspace
+    const size_t img_bytes = (size_t)L.nks * L.nparts * L.opb_part;
+    uint8_t* img = static_cast<uint8_t*>(workspace(st, img_bytes));
+    if (!img) return TL_ENOMEM;
+    a.bimg = img;
+    {
+        constexpr int kEl = PREC == TL_P_TF32 ? 4 : 8;
+        int64_t total = (int64_t)L.nks * L.Jp * (BK / kEl);
+        int grid = (int)((total + 255) / 256);
+        if (grid > sms * 8) grid = sms * 8;
+        ttm_tc_prep_b<PREC><<<grid, 256, 0, st>>>(static_cast<const float*>(B), P.ldb_row,
+                                                  P.ldb_col, (int)P.J, L.Jp, P.nq, L.nks, img,
+                                                  L.opb_part);
+    }
+    static std::once_flag once[6];
+    std::call_once(once[PREC], [&] {
+        cudaFuncSetAttribute(ttm_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024);
+    });
+    int grid = (int)(a.ntiles < sms ? a.ntiles : sms);
+    ttm_tc_kernel<PREC><<<grid, kThreads, L.smem, st>>>(map, a);
+    return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
+}
+
+}  // namespace
+
+int ttm_tc_launches(const TtmPlan&) { return 2; }
+
+int launch_ttm_tc(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate,
+                  int num_sms, cudaStream_t st)
+{
+    switch (P.precision) {
+    case TL_P_TF32: return launch_prec<TL_P_TF32>(P, A, B, C, accumulate, num_sms, st);
+    case TL_P_BF16: return launch_prec<TL_P_BF16>(P, A, B, C, accumulate, num_sms, st);
+    case TL_P_BF16X3: return launch_prec<TL_P_BF16X3>(P, A, B, C, accumulate, num_sms, st);
+    default: return TL_EUNSUPPORTED;
+    }
+}
+
+int ttm_tc_status(bool clear)
+{
+    unsigned int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_status, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return TL_ECUDA;
+    }
+    if (clear && v) {
+        unsigned int z = 0;
+        cudaMemcpyToSymbol(g_tc_status, &z, sizeof z);
+    }
+    return v ? TL_ETIMEOUT : TL_OK;
+}
 
 }  // namespace tl

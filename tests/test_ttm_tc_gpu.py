@@ -1,0 +1,131 @@
+"""GPU parity of the tcgen05 tensor-core ttm (Sec. 5.2 Eq. 25) against the FP64
+oracle, for TF32, BF16 and split-BF16x3 products with FP32 accumulation.
+
+Bars (relative Frobenius error against the FP64 oracle on the unrounded FP32
+inputs): split-BF16x3 <= 1e-5, BF16 <= 1e-2, TF32 <= 1e-2.  Small integers
+are exact in BF16 and TF32 and their sums stay below 2^24, so integer-valued
+inputs must come out bit-exact in every precision: that pins the kernel's
+row / column / k mapping independently of rounding."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import get, put, rel_err, to_dev, ttm_case
+
+pytestmark = pytest.mark.gpu
+
+PREC = {"tf32": 3, "bf16": 4, "bf16x3": 5}
+TOL = {"tf32": 1e-2, "bf16": 1e-2, "bf16x3": 1e-5}
+
+# (shape, q, layout): ROW = contraction contiguous, COL = fastest output mode contiguous
+SHAPES = [
+    ((64, 33, 17), 1, (1, 2, 3)),        # ROW, M = 561 (ragged tile)
+    ((96, 40, 8), 1, (1, 2, 3)),         # ROW, nq = 96 (3 stages)
+    ((48, 300), 1, (1, 2)),              # ROW, nq = 48 (ragged k stage)
+    ((7, 6, 128, 5), 3, (3, 1, 2, 4)),   # ROW via layout: mode 3 fastest
+    ((200, 48, 3), 2, (1, 2, 3)),        # COL, inner 200 (ragged), 3 outer
+    ((256, 64, 2), 2, (1, 2, 3)),        # COL, exact tiles
+    ((128, 100), 2, (1, 2)),             # COL, one outer index, nq = 100
+    ((20, 152, 36), 1, (2, 1, 3)),       # COL via layout: mode 2 fastest, q = 1
+]
+JS = [16, 40, 128, 200, 256, 300, 512]
+
+
+def plan_kernel(tl, A, n, pi, q, J, C, prec):
+    nout = tuple(J if r == q - 1 else x for r, x in enumerate(n))
+    rc, js = tl.tl_plan_describe(tl.TL_OP_TTM, tl.Desc(A, n, pi), None, q, J, prec, 0,
+                                 tl.Desc(C, nout, pi))
+    assert rc == 0
+    return json.loads(js)
+
+
+@pytest.mark.parametrize("prec", sorted(PREC))
+@pytest.mark.parametrize("case", range(len(SHAPES)))
+def test_tc_integer_inputs_bit_exact(tl, cuda_dev, prec, case):
+    n, q, pi = SHAPES[case]
+    g = synth.rng(6000 + case)
+    X = synth.integers(n, 6100 + case)
+    for J in (JS[case % len(JS)], 48):
+        Bm = synth.integers((J, n[q - 1]), 6200 + case + J)
+        A = put(X, pi, cuda_dev, "f32")
+        C = torch.empty(int(np.prod(n)) // n[q - 1] * J, dtype=torch.float32, device=cuda_dev)
+        P = plan_kernel(tl, A, n, pi, q, J, C, PREC[prec])
+        assert P["kernel"] == "ttm_tc", P
+        got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pi, "f32", precision=PREC[prec])
+        np.testing.assert_array_equal(got, ref)
+    assert tl.tl_device_status() == tl.TL_OK
+
+
+@pytest.mark.parametrize("prec", sorted(PREC))
+@pytest.mark.parametrize("J", JS)
+def test_tc_random_within_tolerance(tl, cuda_dev, prec, J):
+    for case, (n, q, pi) in enumerate(SHAPES):
+        X = synth.normal(n, 6300 + case, dtype=np.float64)
+        Bm = synth.normal((J, n[q - 1]), 6400 + case, dtype=np.float64)
+        got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pi, "f32", precision=PREC[prec])
+        err = rel_err(got, ref)
+        assert err <= TOL[prec], (n, q, J, err)
+    assert tl.tl_device_status() == tl.TL_OK
+
+
+@pytest.mark.parametrize("prec", sorted(PREC))
+def test_tc_accumulate_and_other_output_layout(tl, cuda_dev, prec):
+    n, q, pi = (64, 33, 17), 1, (1, 2, 3)
+    X = synth.normal(n, 6500, dtype=np.float64)
+    Bm = synth.normal((72, 64), 6501, dtype=np.float64)
+    C0 = synth.normal((72, 33, 17), 6502, dtype=np.float64)
+    got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pi, "f32", precision=PREC[prec],
+                        accumulate=True, C0=C0)
+    assert rel_err(got, ref) <= TOL[prec]
+    # an output layout the tensor-core path does not take falls back to SIMT
+    got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, (3, 2, 1), "f32", precision=PREC[prec])
+    assert rel_err(got, ref) <= TOL[prec]
+
+
+def test_tc_bf16x3_beats_bf16_by_orders(tl, cuda_dev):
+    n, q, pi = (256, 64, 4), 2, (1, 2, 3)
+    X = synth.normal(n, 6600, dtype=np.float64)
+    Bm = synth.normal((128, 64), 6601, dtype=np.float64)
+    errs = {}
+    for prec in PREC:
+        got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pi, "f32", precision=PREC[prec])
+        errs[prec] = rel_err(got, ref)
+    assert errs["bf16x3"] * 100 < errs["bf16"], errs
+    assert errs["tf32"] < errs["bf16"], errs
+
+
+@pytest.fixture(scope="module")
+def scale_tensors(cuda_dev):
+    case = synth.scale_case()
+    n = case.n
+    memF = case.mem_first
+    X = synth.from_memory(memF, n, synth.first_order(4))
+    memL = synth.to_memory(X, synth.last_order(4))
+    return case, memF, memL, to_dev(memF, cuda_dev, "f32"), to_dev(memL, cuda_dev, "f32")
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_tc_full_scale_sampled(tl, cuda_dev, scale_tensors, prec):
+    case, memF, memL, AF, AL = scale_tensors
+    n = case.n
+    g = synth.rng(6700)
+    C = torch.empty(128 ** 4, dtype=torch.float32, device=cuda_dev)
+    for pi, mem, Ad in ((synth.first_order(4), memF, AF), (synth.last_order(4), memL, AL)):
+        wA = oracle.strides(n, pi)
+        for q in range(1, 5):
+            Bm = case.matrices[q - 1]
+            Bt = to_dev(Bm.reshape(-1), cuda_dev, "f32")
+            P = plan_kernel(tl, Ad, n, pi, q, 128, C, PREC[prec])
+            assert P["kernel"] == "ttm_tc", (pi, q, P)
+            tl.check(tl.tl_ttm(tl.Desc(Ad, n, pi), Bt, 128, 128, 1, q, tl.Desc(C, n, pi),
+                               PREC[prec]))
+            torch.cuda.synchronize()
+            got = get(C, n, pi)
+            idx = np.stack([g.integers(0, x, size=4000) for x in n], axis=1)
+            ref = oracle.ttm_at(mem, n, wA, q, Bm.reshape(-1), 128, 1, idx)
+            assert rel_err(got[tuple(idx.T)], ref) <= TOL[prec], (pi, q)
+    assert tl.tl_device_status() == tl.TL_OK
