@@ -11,8 +11,11 @@
 namespace tl {
 
 // Collapsed iteration space as kernel parameters: dims[0] varies fastest.
+// small != 0 when every linear index fits in 31 bits, so the mapper can use
+// 32-bit division.
 struct DevSpace {
     int nd;
+    int small;
     int64_t n[kMaxDims];
     int64_t s[3][kMaxDims];
 };
@@ -25,6 +28,7 @@ inline DevSpace to_dev(const Space& sp)
         d.n[i] = sp.d[i].n;
         for (int o = 0; o < 3; ++o) d.s[o][i] = sp.d[i].s[o];
     }
+    d.small = sp.count() < (int64_t(1) << 31) ? 1 : 0;
     return d;
 }
 
@@ -37,6 +41,24 @@ __device__ __forceinline__ void map_offsets(const DevSpace& sp, int64_t g, int64
 {
 #pragma unroll
     for (int o = 0; o < NOPS; ++o) off[o] = 0;
+    if (sp.small) {
+        uint32_t gs = (uint32_t)g;
+        for (int d = 0; d < sp.nd; ++d) {
+            uint32_t ext = (uint32_t)(d == 0 ? sp.n[0] / vec0 : sp.n[d]);
+            uint32_t i;
+            if (d == sp.nd - 1) {
+                i = gs;
+            } else {
+                uint32_t qd = gs / ext;
+                i = gs - qd * ext;
+                gs = qd;
+            }
+            int64_t ii = d == 0 ? (int64_t)i * vec0 : (int64_t)i;
+#pragma unroll
+            for (int o = 0; o < NOPS; ++o) off[o] += ii * sp.s[o][d];
+        }
+        return;
+    }
     for (int d = 0; d < sp.nd; ++d) {
         int64_t ext = d == 0 ? sp.n[0] / vec0 : sp.n[d];
         int64_t i;

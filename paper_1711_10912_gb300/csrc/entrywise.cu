@@ -179,6 +179,98 @@ __global__ void __launch_bounds__(kThreads) ew_tile_kernel(const EwArgs a, int64
     }
 }
 
+// Vectorised variant of the tile kernel: TILE x TILE elements (64 for FP32,
+// 32 for FP64), 16-byte global accesses along each operand's unit-stride
+// dim, and every global load of a tile issued before the shared-memory
+// hand-off.  Chosen by the planner when extents and strides allow 16-byte
+// vectors for all three operands.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) ew_tile_vec_kernel(const EwArgs a, int64_t tiles0,
+                                                               int64_t tiles1, int64_t batch)
+{
+    constexpr int VEC = 16 / sizeof(T);
+    constexpr int TILE = 16 * VEC;
+    constexpr int CH = TILE / VEC;          // vectors per tile row (16)
+    constexpr int RPP = kThreads / CH;      // tile rows per pass (16)
+    constexpr int NP = TILE / RPP;          // passes
+    __shared__ T tA[TILE][TILE + 1];
+    __shared__ T tB[TILE][TILE + 1];
+    const T* __restrict__ A = static_cast<const T*>(a.A);
+    const T* __restrict__ B = static_cast<const T*>(a.B);
+    T* __restrict__ C = static_cast<T*>(a.C);
+    const T alpha = (T)a.alpha;
+    const bool unary = (a.op == TL_COPY || a.op == TL_SCALE);
+    const int t = a.tdim;
+    const int ch = threadIdx.x % CH, rr = threadIdx.x / CH;
+    const int64_t n0 = a.sp.n[0], nt = a.sp.n[t];
+    const bool stageA = a.sp.s[0][t] < a.sp.s[0][0];
+    const bool stageB = !unary && a.sp.s[1][t] < a.sp.s[1][0];
+    const int64_t total = tiles0 * tiles1 * batch;
+    for (int64_t blk = blockIdx.x; blk < total; blk += gridDim.x) {
+        int64_t bt0 = blk % tiles0;
+        int64_t rest = blk / tiles0;
+        int64_t bt1 = rest % tiles1;
+        int64_t bz = rest / tiles1;
+        int64_t base[3] = {0, 0, 0};
+        {
+            int64_t g = bz;
+            for (int d = 1; d < a.sp.nd; ++d) {
+                if (d == t) continue;
+                int64_t i = g % a.sp.n[d];
+                g /= a.sp.n[d];
+#pragma unroll
+                for (int o = 0; o < 3; ++o) base[o] += i * a.sp.s[o][d];
+            }
+        }
+        const int64_t i0b = bt0 * TILE, itb = bt1 * TILE;
+        T xa[NP][VEC], xb[NP][VEC];
+        __syncthreads();
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            // staged operands: vectors along t; direct operands: along dim 0
+            const int64_t i0s = i0b + rr + p * RPP, its = itb + ch * VEC;
+            const int64_t i0d = i0b + ch * VEC, itd = itb + rr + p * RPP;
+            if (stageA) {
+                if (i0s < n0 && its < nt) {
+                    T x[VEC];
+                    vload_stream<T, VEC>(A + base[0] + i0s * a.sp.s[0][0] + its, x);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) tA[ch * VEC + e][rr + p * RPP] = x[e];
+                }
+            } else if (i0d < n0 && itd < nt) {
+                vload_stream<T, VEC>(A + base[0] + i0d + itd * a.sp.s[0][t], xa[p]);
+            }
+            if (!unary) {
+                if (stageB) {
+                    if (i0s < n0 && its < nt) {
+                        T x[VEC];
+                        vload_stream<T, VEC>(B + base[1] + i0s * a.sp.s[1][0] + its, x);
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) tB[ch * VEC + e][rr + p * RPP] = x[e];
+                    }
+                } else if (i0d < n0 && itd < nt) {
+                    vload_stream<T, VEC>(B + base[1] + i0d + itd * a.sp.s[1][t], xb[p]);
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const int64_t i0 = i0b + ch * VEC, it = itb + rr + p * RPP;
+            if (i0 < n0 && it < nt) {
+                T r[VEC];
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    T x = stageA ? tA[rr + p * RPP][ch * VEC + e] : xa[p][e];
+                    T y = unary ? T(0) : (stageB ? tB[rr + p * RPP][ch * VEC + e] : xb[p][e]);
+                    r[e] = apply<T>(a.op, x, y, alpha);
+                }
+                vstore<T, VEC>(C + base[2] + i0 + it * a.sp.s[2][t], r);
+            }
+        }
+    }
+}
+
 int grid_for(int64_t threads, int num_sms)
 {
     int64_t blocks = (threads + kThreads - 1) / kThreads;
@@ -206,13 +298,15 @@ int launch_typed(const EwPlan& P, const void* A, const void* B, double alpha, vo
         if (P.vec == V) ew_flat_kernel<T, V><<<grid, kThreads, 0, st>>>(a);
         else ew_flat_kernel<T, 1><<<grid, kThreads, 0, st>>>(a);
     } else if (P.kernel == K_EW_TILE) {
-        int64_t tiles0 = (P.sp.d[0].n + kTile - 1) / kTile;
-        int64_t tiles1 = (P.sp.d[P.tdim].n + kTile - 1) / kTile;
+        const int tile = P.vec > 1 ? 16 * V : kTile;
+        int64_t tiles0 = (P.sp.d[0].n + tile - 1) / tile;
+        int64_t tiles1 = (P.sp.d[P.tdim].n + tile - 1) / tile;
         int64_t batch = P.N / (P.sp.d[0].n * P.sp.d[P.tdim].n);
         int64_t total = tiles0 * tiles1 * batch;
         int64_t cap = (int64_t)num_sms * 8;
         int grid = (int)(total < cap ? total : cap);
-        ew_tile_kernel<T><<<grid, kThreads, 0, st>>>(a, tiles0, tiles1, batch);
+        if (P.vec > 1) ew_tile_vec_kernel<T><<<grid, kThreads, 0, st>>>(a, tiles0, tiles1, batch);
+        else ew_tile_kernel<T><<<grid, kThreads, 0, st>>>(a, tiles0, tiles1, batch);
     } else {
         ew_generic_kernel<T><<<grid_for(P.N, num_sms), kThreads, 0, st>>>(a);
     }

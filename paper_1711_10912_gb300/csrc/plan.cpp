@@ -300,6 +300,21 @@ int plan_entrywise(int32_t op, const Tensor& A, const Tensor* B, const Tensor& C
     if (t > 0 && P.sp.d[0].s[2] == 1) {
         P.kernel = K_EW_TILE;
         P.tdim = t;
+        // 16-byte vectors: each operand contiguous along dim 0 (read in the
+        // write phase) or along dim t (staged), every other stride and both
+        // tiled extents multiples of the vector width, 16-byte aligned bases
+        const Space& sp = P.sp;
+        bool v = sp.d[0].n % V == 0 && sp.d[t].n % V == 0 && aligned(C.data, 16) &&
+                 aligned(A.data, 16) && (!B || aligned(B->data, 16));
+        for (int o = 0; o < 3 && v; ++o) {
+            if (o == 1 && !B) continue;
+            bool staged = o < 2 && sp.d[t].s[o] < sp.d[0].s[o];
+            int unit = staged ? t : 0, other = staged ? 0 : t;
+            v = sp.d[unit].s[o] == 1 && sp.d[other].s[o] % V == 0;
+            for (int d = 1; d < sp.nd && v; ++d)
+                if (d != t) v = sp.d[d].s[o] % V == 0;
+        }
+        P.vec = v ? V : 1;
     } else {
         P.kernel = K_EW_GENERIC;
     }

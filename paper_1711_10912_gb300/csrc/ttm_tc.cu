@@ -235,7 +235,7 @@ struct TcArgs {
     int64_t scq;             // C stride of j
     uint32_t a_stage_bytes;  // FP32 staging tile
     uint32_t opa_part_bytes, opb_part_bytes;
-    uint32_t off_stg, off_op, op_stage_bytes, off_bar;
+    uint32_t off_stg, off_op, op_stage_bytes, off_bar, off_epi;
 };
 
 struct Bars {
@@ -485,29 +485,43 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
         // ------------------------------------------------------ epilogue
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
+        // per-warp 32 x 33 staging tile: rows are TMEM lanes, columns j
+        float* tile = reinterpret_cast<float*>(sbase + a.off_epi) + (warp - 6) * 32 * 33;
+        // j contiguous in C (and not i): transpose so that lanes run along j
+        const bool j_fast = (a.scq == 1);
         Pipe acc;
         bool ok = true;
-        for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+        for (int64_t tile_id = blockIdx.x; tile_id < a.ntiles && ok; tile_id += gridDim.x) {
             if (!(ok = mbar_wait(bars.acc_full + 8 * acc.idx, acc.phase))) break;
             tc_fence_after();
-            bool valid;
-            int64_t offc;
+            int64_t rbase, obase = 0, nrows;
             if (a.variant == V_COL) {
-                int64_t o = tile / a.tiles_per_o;
-                int64_t i = (tile % a.tiles_per_o) * BM + row;
-                valid = i < a.M;
-                offc = o * a.sc_o + i * a.sc_m;
+                int64_t o = tile_id / a.tiles_per_o;
+                rbase = (tile_id % a.tiles_per_o) * BM + quarter * 32;
+                obase = o * a.sc_o;
             } else {
-                int64_t m = tile * BM + row;
-                valid = m < a.M;
-                offc = m * a.sc_m;
+                rbase = tile_id * BM + quarter * 32;
             }
+            nrows = a.M - rbase;               // rows of this warp that exist (may be <= 0)
             const uint32_t tcol = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc.idx * acc_cols;
             for (int c0 = 0; c0 < a.Jp; c0 += 32) {
                 float v[32];
                 tmem_ld32(tcol + c0, v);
-                if (valid) {
-                    float* pc = a.C + offc;
+                if (j_fast) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = v[j];
+                    __syncwarp();
+                    const int jg = c0 + lane;
+                    if (jg < a.J) {
+                        for (int r = 0; r < 32 && r < nrows; ++r) {
+                            float* p = a.C + obase + (rbase + r) * a.sc_m + jg;
+                            float x = tile[r * 33 + lane];
+                            *p = a.accumulate ? *p + x : x;
+                        }
+                    }
+                    __syncwarp();
+                } else if (lane < nrows) {
+                    float* pc = a.C + obase + (rbase + lane) * a.sc_m;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         int jg = c0 + j;
@@ -599,7 +613,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 struct Layout {
     int nparts, esize, Jp, nks, ns_stg, ns_op, nacc;
-    uint32_t a_stage, opa_part, opb_part, op_stage, off_stg, off_op, off_bar, smem;
+    uint32_t a_stage, opa_part, opb_part, op_stage, off_stg, off_op, off_epi, off_bar, smem;
 };
 
 Layout layout_for(const TtmPlan& P)
@@ -614,14 +628,20 @@ Layout layout_for(const TtmPlan& P)
     L.opa_part = BM * BK * L.esize;
     L.opb_part = (uint32_t)L.Jp * BK * L.esize;
     L.op_stage = L.nparts * (L.opa_part + L.opb_part);
-    const uint32_t budget = 227 * 1024 - 1024 - 256;    // alignment slack + barriers
-    L.ns_stg = 4;
-    L.ns_op = 4;
-    while (L.ns_op > 2 && L.ns_stg * L.a_stage + L.ns_op * L.op_stage > budget) --L.ns_op;
-    while (L.ns_stg > 2 && L.ns_stg * L.a_stage + L.ns_op * L.op_stage > budget) --L.ns_stg;
+    const uint32_t epi = 4 * 32 * 33 * 4;                // epilogue transpose tiles
+    const uint32_t budget = 227 * 1024 - 1024 - 512 - epi;   // alignment slack + barriers
+    // FP32 staging keeps the HBM bytes in flight; the operand ring only has
+    // to cover the convert -> MMA hand-off
+    for (L.ns_op = 3; L.ns_op >= 2; --L.ns_op) {
+        int64_t room = (int64_t)budget - (int64_t)L.ns_op * L.op_stage;
+        L.ns_stg = room > 0 ? (int)(room / L.a_stage) : 0;
+        if (L.ns_stg > 8) L.ns_stg = 8;
+        if (L.ns_stg >= 2) break;
+    }
     L.off_stg = 0;
     L.off_op = L.ns_stg * L.a_stage;
-    L.off_bar = L.off_op + L.ns_op * L.op_stage;
+    L.off_epi = L.off_op + L.ns_op * L.op_stage;
+    L.off_bar = L.off_epi + epi;
     L.smem = L.off_bar + 8 * (2 * L.ns_stg + 2 * L.ns_op + 4) + 16 + 1024;
     // more than half of the SM's shared memory keeps one CTA per SM, so no
     // two CTAs ever wait on each other for the 512 TMEM columns
@@ -634,7 +654,7 @@ int launch_prec(const TtmPlan& P, const void* A, const void* B, void* C, int acc
                 cudaStream_t st)
 {
     const Layout L = layout_for(P);
-    if (L.smem > 227 * 1024) return TL_EUNSUPPORTED;
+    if (L.smem > 227 * 1024 || L.ns_stg < 2 || L.ns_op < 2) return TL_EUNSUPPORTED;
     auto enc = encode_fn();
     if (!enc) return TL_ECUDA;
 
@@ -659,6 +679,7 @@ int launch_prec(const TtmPlan& P, const void* A, const void* B, void* C, int acc
     a.off_op = L.off_op;
     a.op_stage_bytes = L.op_stage;
     a.off_bar = L.off_bar;
+    a.off_epi = L.off_epi;
 
     CUtensorMap map;
     CUresult cr;

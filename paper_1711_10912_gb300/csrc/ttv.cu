@@ -35,85 +35,92 @@ struct TtvArgs {
 
 constexpr int kThreads = 256;
 
-template <typename T, int VEC, int L, int R>
+// Sums 4 per-lane partials over groups of L lanes with a halving butterfly
+// (6 shuffles for L = 32 instead of 4 x 5): afterwards the lane with
+// sub-lane index s holds the total of row 2*(s >= L/2) + ((s & L/4) != 0).
+template <typename T, int L>
+__device__ __forceinline__ T reduce4(T a0, T a1, T a2, T a3, int sub)
+{
+    constexpr int h = L / 2, h2 = L / 4;
+    const bool up = (sub & h) != 0;
+    T y0 = __shfl_xor_sync(0xffffffffu, up ? a0 : a2, h);
+    T y1 = __shfl_xor_sync(0xffffffffu, up ? a1 : a3, h);
+    T k0 = (up ? a2 : a0) + y0;
+    T k1 = (up ? a3 : a1) + y1;
+    const bool up2 = (sub & h2) != 0;
+    T y = __shfl_xor_sync(0xffffffffu, up2 ? k0 : k1, h2);
+    T r = (up2 ? k1 : k0) + y;
+#pragma unroll
+    for (int m = h2 / 2; m >= 1; m /= 2) r += __shfl_xor_sync(0xffffffffu, r, m);
+    return r;
+}
+
+template <typename T, int VEC, int L>
 __global__ void __launch_bounds__(kThreads) ttv_row_kernel(const TtvArgs a)
 {
+    constexpr int R = 4;
     const T* __restrict__ A = static_cast<const T*>(a.A);
     const T* __restrict__ b = static_cast<const T*>(a.b);
     const int lane = threadIdx.x & 31;
-    const int sub = lane % L;
+    const int sub = lane & (L - 1);
     const int64_t group = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / L;
     const int64_t ngroups = (int64_t)gridDim.x * kThreads / L;
-    const int64_t work = a.nout * a.splits;
-    // every lane of a warp runs the same number of iterations so the
-    // shuffles below always see a converged warp
-    const int64_t iters = (work + (int64_t)R * ngroups - 1) / ((int64_t)R * ngroups);
-    for (int64_t it = 0; it < iters; ++it) {
-        T acc[R];
-        int64_t item[R], offA[R];
-        bool ok[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            item[r] = (it * R + r) * ngroups + group;
-            ok[r] = item[r] < work;
-            acc[r] = T(0);
-            offA[r] = 0;
-        }
-        int64_t k0[R], k1[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            int64_t row = ok[r] ? item[r] % a.nout : 0;
-            int64_t s = ok[r] ? item[r] / a.nout : 0;
-            int64_t off[2];
-            map_offsets<1>(a.out, row, 1, off);
-            offA[r] = off[0];
-            k0[r] = s * a.kchunk;
-            k1[r] = ok[r] ? min(a.nq, k0[r] + a.kchunk) : k0[r];
-        }
-        // all rows of this iteration share the same k extent except at the
-        // last split; walk the longest and guard per row
-        int64_t kspan = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) kspan = max(kspan, k1[r] - k0[r]);
-        for (int64_t kk = (int64_t)sub * VEC; kk < kspan; kk += (int64_t)L * VEC) {
-            T va[R][VEC];
+    const int64_t step = (int64_t)R * ngroups;
+    // every lane of a warp runs the same iterations, so the shuffles always
+    // see a converged warp
+    const int64_t iters = (a.nout + step - 1) / step;
+    for (int s = 0; s < a.splits; ++s) {
+        const int64_t k0 = (int64_t)s * a.kchunk;
+        const int64_t klen = min(a.nq - k0, a.kchunk);
+        for (int64_t it = 0; it < iters; ++it) {
+            int64_t row[R], offA[R];
+            bool ok[R];
+            T acc[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                if (kk < k1[r] - k0[r]) {
-                    vload_stream<T, VEC>(A + offA[r] + k0[r] + kk, va[r]);
-                } else {
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) va[r][v] = T(0);
-                }
+                row[r] = (it * R + r) * ngroups + group;
+                ok[r] = row[r] < a.nout;
+                acc[r] = T(0);
+                int64_t off[1] = {0};
+                if (ok[r]) map_offsets<1>(a.out, row[r], 1, off);
+                offA[r] = off[0] + k0;
             }
+            for (int64_t kk = (int64_t)sub * VEC; kk < klen; kk += (int64_t)L * VEC) {
+                T vb[VEC];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (kk < k1[r] - k0[r]) {
+                for (int v = 0; v < VEC; ++v) vb[v] = __ldg(b + (k0 + kk + v) * a.incb);
+                T va[R][VEC];
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v)
-                        acc[r] = fma(va[r][v], __ldg(b + (k0[r] + kk + v) * a.incb), acc[r]);
+                for (int r = 0; r < R; ++r) {
+                    if (ok[r]) {
+                        vload_stream<T, VEC>(A + offA[r] + kk, va[r]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) va[r][v] = T(0);
+                    }
                 }
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[r] = fma(va[r][v], vb[v], acc[r]);
             }
-        }
-        // scalar tail when VEC == 1 handled by the loop; reduce within groups
+            const T tot = reduce4<T, L>(acc[0], acc[1], acc[2], acc[3], sub);
+            if ((sub & (L / 4 - 1)) == 0) {
+                const int rs = 2 * ((sub & (L / 2)) != 0) + ((sub & (L / 4)) != 0);
+                int64_t rw = 0;
+                bool okw = false;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-#pragma unroll
-            for (int m = L / 2; m >= 1; m /= 2) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], m);
-        }
-        if (sub == 0) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (!ok[r]) continue;
-                int64_t row = item[r] % a.nout;
-                int64_t s = item[r] / a.nout;
-                if (a.splits > 1) {
-                    static_cast<T*>(a.ws)[s * a.nout + row] = acc[r];
-                } else {
-                    int64_t off[2];
-                    map_offsets<2>(a.out, row, 1, off);
-                    T* c = static_cast<T*>(a.C) + off[1];
-                    *c = a.accumulate ? *c + acc[r] : acc[r];
+                for (int r = 0; r < R; ++r)
+                    if (r == rs) { rw = row[r]; okw = ok[r]; }
+                if (okw) {
+                    if (a.splits > 1) {
+                        static_cast<T*>(a.ws)[(int64_t)s * a.nout + rw] = tot;
+                    } else {
+                        int64_t off[2];
+                        map_offsets<2>(a.out, rw, 1, off);
+                        T* c = static_cast<T*>(a.C) + off[1];
+                        *c = a.accumulate ? *c + tot : tot;
+                    }
                 }
             }
         }
@@ -220,10 +227,9 @@ int launch_typed(const TtvPlan& P, const void* A, const void* b, void* C, void* 
     a.accumulate = accumulate;
     constexpr int V = 16 / sizeof(T);
     if (P.kernel == K_TTV_ROW) {
-        constexpr int R = 4;
-        int64_t threads = (P.nout * P.splits + R - 1) / R * P.lanes;
+        int64_t threads = (P.nout + 3) / 4 * P.lanes;
         int grid = grid_for(threads, num_sms);
-#define TL_ROW(VV, LL) ttv_row_kernel<T, VV, LL, R><<<grid, kThreads, 0, st>>>(a)
+#define TL_ROW(VV, LL) ttv_row_kernel<T, VV, LL><<<grid, kThreads, 0, st>>>(a)
         if (P.vec == V) {
             switch (P.lanes) {
             case 32: TL_ROW(V, 32); break;

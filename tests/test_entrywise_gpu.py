@@ -50,7 +50,8 @@ def test_entrywise_random_layouts_bit_exact(tl, cuda_dev, dtype, op, seed):
     np.testing.assert_array_equal(got, ref)
 
 
-@pytest.mark.parametrize("shape", [(1000, 77, 3), (33, 65, 17), (257, 129), (5, 4, 3, 200)])
+@pytest.mark.parametrize("shape", [(1000, 77, 3), (33, 65, 17), (257, 129), (5, 4, 3, 200),
+                                   (100, 68, 12), (36, 20, 64), (128, 4, 132)])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_entrywise_first_last_mixes_ragged(tl, cuda_dev, shape, dtype):
     p = len(shape)
@@ -108,3 +109,17 @@ def test_entrywise_full_scale_sampled(tl, cuda_dev):
     torch.cuda.synchronize()
     got = C.cpu().numpy()
     np.testing.assert_array_equal(got, (memF.astype(np.float64) * 2).astype(np.float32))
+
+
+def test_entrywise_vector_tile_path_is_taken(tl, cuda_dev):
+    # extents and strides that allow 16-byte vectors select the vector tile
+    import json
+    for dtype in ("f32", "f64"):
+        n = (100, 68, 12)
+        A = put(np.zeros(n), (1, 2, 3), cuda_dev, dtype)
+        B = put(np.zeros(n), (3, 2, 1), cuda_dev, dtype)
+        C = torch.empty_like(A)
+        rc, js = tl.tl_plan_describe(tl.TL_OP_ENTRYWISE, tl.Desc(A, n, (1, 2, 3)),
+                                     tl.Desc(B, n, (3, 2, 1)), 0, 0, 0, 0, tl.Desc(C, n))
+        P = json.loads(js)
+        assert P["kernel"] == "ew_tile" and P["vec"] == (4 if dtype == "f32" else 2), P
