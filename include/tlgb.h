@@ -198,6 +198,15 @@ uint64_t tl_launch_count(void);
 int tl_device_status(void* stream);
 
 /*
+ * tl_selftest_wait_timeout -- launches one tiny kernel whose thread waits on
+ * a barrier that nothing completes, with a limit of about `limit_us`
+ * microseconds; the wait gives up, records the timeout exactly as the
+ * pipelined kernels do and returns.  A following tl_device_status() reports
+ * TL_ETIMEOUT.  Exercises the timeout path without hanging the GPU.
+ */
+int tl_selftest_wait_timeout(double limit_us, void* stream);
+
+/*
  * tl_plan_describe -- host-only: validates the arguments of a ttv (op 0),
  * ttm (op 1) or entrywise (op 2) call exactly as the entry point would and
  * writes a one-line JSON description of the collapsed iteration space and
@@ -239,6 +248,49 @@ typedef struct tl_op {
     tl_tensor A, B, C;
 } tl_op;
 
+/*
+ * Batched persistent launch: many operations of uneven order, extents and
+ * layout in one launch.  tl_batch_create validates and plans every
+ * operation (exactly as the single-call entry points would), cuts each into
+ * work units and uploads one descriptor table; tl_batch_run enqueues one
+ * persistent kernel that takes units from an atomic counter (operations it
+ * does not take, such as tensor-core ttm, run through their own kernels).
+ * flags: TL_BATCH_GRAPH captures the launch into a CUDA graph on the first
+ * run and replays it afterwards; TL_BATCH_TUNE picks each shape class's
+ * unit size and per-unit code by timing the candidates once (on `stream`,
+ * at creation) and caching the choice in the file $TL_TUNE_CACHE (default
+ * ~/.cache/tlgb_tune.txt).  tl_batch_create allocates the table and
+ * synchronises `stream`; the data pointers of the operations must stay
+ * valid for every run.  tl_batch_describe writes a JSON summary.
+ */
+typedef struct tl_batch tl_batch;
+#define TL_BATCH_GRAPH 1
+#define TL_BATCH_TUNE  2
+int tl_batch_create(const struct tl_op* ops, size_t count, int32_t flags, void* stream,
+                    tl_batch** out);
+int tl_batch_run(tl_batch* batch, void* stream);
+int tl_batch_destroy(tl_batch* batch);
+int tl_batch_describe(const tl_batch* batch, char* buf, size_t buflen);
+
+/*
+ * Overrides the per-unit code of every operation of one kind in a batch
+ * (for tuning experiments and tests): kind TL_OP_TTV with variant
+ * TL_BV_TTV_COL (a thread per output) or TL_BV_TTV_ROW4/8/32 (4, 8 or 32
+ * lanes per output), TL_OP_TTM with TL_BV_TTM_32 / TL_BV_TTM_64 (row tiles),
+ * TL_OP_ENTRYWISE with TL_BV_EW.  `unit` is the outputs per work unit
+ * (ignored for ttm).  Re-uploads the table (synchronising `stream`) and
+ * drops a captured graph.
+ */
+#define TL_BV_TTV_COL   0
+#define TL_BV_TTV_ROW4  1
+#define TL_BV_TTV_ROW8  2
+#define TL_BV_TTV_ROW32 3
+#define TL_BV_TTM_32    4
+#define TL_BV_TTM_64    5
+#define TL_BV_EW        6
+int tl_batch_set_variant(tl_batch* batch, int32_t kind, int32_t variant, int64_t unit,
+                         void* stream);
+
 typedef struct tl_ctx tl_ctx;
 
 /* Context flags */
@@ -269,6 +321,8 @@ int tl_batch_submit(tl_ctx* ctx, const tl_op* ops, size_t count, uint64_t* ticke
 /*
  * tl_poll -- non-blocking status of a ticket: *status = TL_PENDING, TL_OK or
  * a negative error; *latency_ms = submission-to-completion time once done.
+ * A ticket is forgotten once its final status has been returned (by tl_poll
+ * or tl_wait); asking again returns TL_EINVAL.
  */
 int tl_poll(tl_ctx* ctx, uint64_t ticket, int32_t* status, double* latency_ms);
 
@@ -276,7 +330,14 @@ int tl_poll(tl_ctx* ctx, uint64_t ticket, int32_t* status, double* latency_ms);
 int tl_wait(tl_ctx* ctx, uint64_t ticket, double timeout_ms, int32_t* status,
             double* latency_ms);
 
-/* Marks a pending, not yet launched request as cancelled (TL_ECANCELED). */
+/* Counters of a context: the most operand + output bytes ever admitted at
+   once (never above the budget), batches launched and requests completed. */
+int tl_ctx_stats(tl_ctx* ctx, size_t* max_inflight_bytes, uint64_t* batches,
+                 uint64_t* completed);
+
+/* Cancels a request that has not been launched yet (its status becomes
+   TL_ECANCELED and TL_OK is returned); a launched request runs to completion
+   (TL_PENDING is returned). */
 int tl_cancel(tl_ctx* ctx, uint64_t ticket);
 
 #ifdef __cplusplus

@@ -41,6 +41,9 @@ TL_P_DEFAULT, TL_P_F64, TL_P_F32, TL_P_TF32, TL_P_BF16, TL_P_BF16X3 = range(6)
 TL_ADD, TL_SUB, TL_MUL, TL_DIV, TL_COPY, TL_SCALE = range(6)
 TL_OP_TTV, TL_OP_TTM, TL_OP_ENTRYWISE = range(3)
 TL_CTX_PERSISTENT, TL_CTX_GRAPH = 1, 2
+TL_BATCH_GRAPH, TL_BATCH_TUNE = 1, 2
+(TL_BV_TTV_COL, TL_BV_TTV_ROW4, TL_BV_TTV_ROW8, TL_BV_TTV_ROW32, TL_BV_TTM_32, TL_BV_TTM_64,
+ TL_BV_EW) = range(7)
 
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -169,6 +172,16 @@ def _declare(_lib):
     _lib.tl_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double,
                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
     _lib.tl_cancel.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+    _lib.tl_ctx_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t),
+                                  ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+    _lib.tl_batch_create.argtypes = [ctypes.POINTER(tl_op), ctypes.c_size_t, ctypes.c_int32,
+                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    _lib.tl_batch_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    _lib.tl_batch_destroy.argtypes = [ctypes.c_void_p]
+    _lib.tl_batch_describe.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]
+    _lib.tl_batch_set_variant.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int64, ctypes.c_void_p]
+    _lib.tl_selftest_wait_timeout.argtypes = [ctypes.c_double, ctypes.c_void_p]
 
 
 load_library()
@@ -263,6 +276,58 @@ def tl_wait(ctx, ticket: int, timeout_ms: float = 60000.0) -> tuple:
 
 def tl_cancel(ctx, ticket: int) -> int:
     return _lib.tl_cancel(ctx, int(ticket))
+
+
+def tl_ctx_stats(ctx) -> tuple:
+    m, b, c = ctypes.c_size_t(), ctypes.c_uint64(), ctypes.c_uint64()
+    rc = _lib.tl_ctx_stats(ctx, ctypes.byref(m), ctypes.byref(b), ctypes.byref(c))
+    return rc, m.value, b.value, c.value
+
+
+def tl_batch_create(ops, flags: int = 0, stream=None) -> tuple:
+    arr = (tl_op * max(len(ops), 1))(*ops)
+    out = ctypes.c_void_p()
+    rc = _lib.tl_batch_create(arr, len(ops), int(flags), _stream(stream), ctypes.byref(out))
+    return rc, out
+
+
+def tl_batch_run(batch, stream=None) -> int:
+    return _lib.tl_batch_run(batch, _stream(stream))
+
+
+def tl_batch_destroy(batch) -> int:
+    return _lib.tl_batch_destroy(batch)
+
+
+def tl_batch_describe(batch) -> tuple:
+    buf = ctypes.create_string_buffer(1024)
+    rc = _lib.tl_batch_describe(batch, buf, len(buf))
+    return rc, buf.value.decode()
+
+
+def tl_batch_set_variant(batch, kind: int, variant: int, unit: int, stream=None) -> int:
+    return _lib.tl_batch_set_variant(batch, int(kind), int(variant), int(unit), _stream(stream))
+
+
+def tl_selftest_wait_timeout(limit_us: float, stream=None) -> int:
+    return _lib.tl_selftest_wait_timeout(float(limit_us), _stream(stream))
+
+
+def make_op(kind: int, A: Desc, C: Desc, q: int = 0, vec=None, B: Desc = None, J: int = 0,
+            ldb_row: int = 0, ldb_col: int = 1, incb: int = 1, precision: int = TL_P_DEFAULT,
+            accumulate: int = 0, entry_op: int = TL_ADD, alpha: float = 1.0) -> tl_op:
+    """Fills a tl_op; the Desc objects must outlive every use of the op."""
+    o = tl_op()
+    o.kind, o.entry_op, o.precision, o.accumulate = int(kind), int(entry_op), int(precision), \
+        int(accumulate)
+    o.q, o.J, o.ldb_row, o.ldb_col, o.incb, o.alpha = int(q), int(J), int(ldb_row), int(ldb_col), \
+        int(incb), float(alpha)
+    o.vec = ctypes.c_void_p(_addr(vec))
+    o.A = A.s
+    o.C = C.s
+    if B is not None:
+        o.B = B.s
+    return o
 
 
 def check(rc: int, what: str = "tl call") -> None:

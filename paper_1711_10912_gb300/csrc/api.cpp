@@ -183,6 +183,13 @@ int tl_version(void) { return 100; }
 
 uint64_t tl_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int tl_selftest_wait_timeout(double limit_us, void* stream)
+{
+    int rc = selftest_wait_timeout(limit_us, static_cast<cudaStream_t>(stream));
+    if (rc == TL_OK) count_launches(1);
+    return rc;
+}
+
 int tl_device_status(void* stream)
 {
     if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return TL_ECUDA;

@@ -1,0 +1,860 @@
+// batch.cu -- many small ttv / ttm / entrywise operations (Sec. 5.2 Eqs. 24-25,
+// Sec. 5.1 Eq. 23) of uneven order, extents and layout in ONE persistent
+// launch.
+//
+// Each operation is planned on the host exactly as a single call would be
+// (validation, Eq. 14 strides, joint mode collapse) and becomes a device
+// descriptor.  Its outputs are cut into work units (a range of outputs for
+// ttv and entrywise, a tile of rows for ttm); a prefix sum over the units of
+// all operations forms one global unit index.  A persistent grid takes units
+// from an atomic counter, looks the owning operation up by binary search and
+// runs the unit with the whole CTA.  The unit size and the per-unit code
+// variant of every shape class are chosen by an autotuner that times the
+// candidates once and caches the winner on disk.  The launch (counter reset
+// + kernel) can be captured into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <sys/stat.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "batch.h"
+#include "device.cuh"
+#include "kernels.h"
+#include "runtime.h"
+
+namespace tl {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBD = 8;              // dims of a collapsed space in a batch descriptor
+
+// Work-unit code variants.
+enum : int32_t {
+    BV_TTV_COL = 0,      // one thread per output, k loop
+    BV_TTV_ROW4 = 1,     // 4 lanes per output (contraction contiguous)
+    BV_TTV_ROW8 = 2,
+    BV_TTV_ROW32 = 3,
+    BV_TTM_32 = 4,       // smem-tiled GEMM tile of 32 rows
+    BV_TTM_64 = 5,       // 64 rows
+    BV_EW = 6,           // one thread per element
+};
+
+struct BOp {
+    int32_t kind, dtype, variant, nd;
+    int32_t eop, accumulate;
+    int64_t count;       // outputs (ttv), rows (ttm) or elements (entrywise)
+    int64_t unit;        // count per work unit
+    int64_t ubegin;      // first global unit of this operation
+    int64_t n[kBD], s0[kBD], s1[kBD], s2[kBD];
+    int64_t nq, saq, incb, J, scq, ldb_row, ldb_col;
+    double alpha;
+    const void* A;
+    const void* B;       // b (ttv), B (ttm), second operand (entrywise)
+    void* C;
+};
+
+__device__ __forceinline__ void bdecode(const BOp& op, int64_t g, int64_t& o0, int64_t& o1,
+                                        int64_t& o2)
+{
+    o0 = o1 = o2 = 0;
+    for (int d = 0; d < op.nd; ++d) {
+        int64_t i;
+        if (d == op.nd - 1) {
+            i = g;
+        } else {
+            int64_t q = g / op.n[d];
+            i = g - q * op.n[d];
+            g = q;
+        }
+        o0 += i * op.s0[d];
+        o1 += i * op.s1[d];
+        o2 += i * op.s2[d];
+    }
+}
+
+template <typename T>
+__device__ void unit_ttv_col(const BOp& op, int64_t e0, int64_t e1)
+{
+    const T* A = static_cast<const T*>(op.A);
+    const T* b = static_cast<const T*>(op.B);
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
+        int64_t oa, oc, unused;
+        bdecode(op, e, oa, oc, unused);
+        const T* pa = A + oa;
+        T acc = T(0);
+        int64_t k = 0;
+        for (; k + 4 <= op.nq; k += 4) {
+            T a0 = __ldg(pa + k * op.saq), a1 = __ldg(pa + (k + 1) * op.saq);
+            T a2 = __ldg(pa + (k + 2) * op.saq), a3 = __ldg(pa + (k + 3) * op.saq);
+            acc = fma(a0, __ldg(b + k * op.incb), acc);
+            acc = fma(a1, __ldg(b + (k + 1) * op.incb), acc);
+            acc = fma(a2, __ldg(b + (k + 2) * op.incb), acc);
+            acc = fma(a3, __ldg(b + (k + 3) * op.incb), acc);
+        }
+        for (; k < op.nq; ++k) acc = fma(__ldg(pa + k * op.saq), __ldg(b + k * op.incb), acc);
+        T* pc = static_cast<T*>(op.C) + oc;
+        *pc = op.accumulate ? *pc + acc : acc;
+    }
+}
+
+template <typename T, int L>
+__device__ void unit_ttv_row(const BOp& op, int64_t e0, int64_t e1)
+{
+    const T* A = static_cast<const T*>(op.A);
+    const T* b = static_cast<const T*>(op.B);
+    const int g = threadIdx.x / L, sub = threadIdx.x % L;
+    constexpr int G = kThreads / L;
+    // uniform trip count so every shuffle sees a converged warp
+    for (int64_t base = e0; base < e1; base += G) {
+        const int64_t e = base + g;
+        const bool ok = e < e1;
+        T acc = T(0);
+        int64_t oa = 0, oc = 0, unused;
+        if (ok) {
+            bdecode(op, e, oa, oc, unused);
+            for (int64_t k = sub; k < op.nq; k += L)
+                acc = fma(__ldg(A + oa + k * op.saq), __ldg(b + k * op.incb), acc);
+        }
+#pragma unroll
+        for (int m = L / 2; m >= 1; m /= 2) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+        if (ok && sub == 0) {
+            T* pc = static_cast<T*>(op.C) + oc;
+            *pc = op.accumulate ? *pc + acc : acc;
+        }
+    }
+}
+
+// Rows [m0, m0 + BM) x all J columns; k staged 16 deep in shared memory.
+template <typename T, int BM>
+__device__ void unit_ttm(const BOp& op, int64_t m0, uint8_t* smem)
+{
+    constexpr int BJ = 64, BK = 16;
+    T (*As)[BM + 1] = reinterpret_cast<T (*)[BM + 1]>(smem);
+    T (*Bs)[BJ + 1] = reinterpret_cast<T (*)[BJ + 1]>(smem + sizeof(T) * BK * (BM + 1));
+    int64_t* offA = reinterpret_cast<int64_t*>(smem + sizeof(T) * BK * (BM + 1 + BJ + 1));
+    int64_t* offC = offA + BM;
+    const T* A = static_cast<const T*>(op.A);
+    const T* B = static_cast<const T*>(op.B);
+    T* C = static_cast<T*>(op.C);
+    const int tid = threadIdx.x, tm = tid & 15, tj = tid >> 4;
+    constexpr int RM = BM / 16;
+    const bool a_kfast = op.saq == 1, b_kfast = op.ldb_col == 1;
+    if (tid < BM) {
+        int64_t oa = 0, oc = 0, unused;
+        if (m0 + tid < op.count) bdecode(op, m0 + tid, oa, oc, unused);
+        offA[tid] = oa;
+        offC[tid] = oc;
+    }
+    for (int64_t j0 = 0; j0 < op.J; j0 += BJ) {
+        T acc[RM][4];
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+        for (int64_t k0 = 0; k0 < op.nq; k0 += BK) {
+            __syncthreads();
+            for (int e = tid; e < BM * BK; e += kThreads) {
+                int mm, kk;
+                if (a_kfast) { kk = e % BK; mm = e / BK; }
+                else { mm = e % BM; kk = e / BM; }
+                int64_t k = k0 + kk;
+                As[kk][mm] = (m0 + mm < op.count && k < op.nq) ? __ldg(A + offA[mm] + k * op.saq) : T(0);
+            }
+            for (int e = tid; e < BJ * BK; e += kThreads) {
+                int jj, kk;
+                if (b_kfast) { kk = e % BK; jj = e / BK; }
+                else { jj = e % BJ; kk = e / BJ; }
+                int64_t j = j0 + jj, k = k0 + kk;
+                Bs[kk][jj] = (j < op.J && k < op.nq) ? __ldg(B + j * op.ldb_row + k * op.ldb_col) : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                T av[RM], bv[4];
+#pragma unroll
+                for (int i = 0; i < RM; ++i) av[i] = As[kk][tm + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tj + 16 * j];
+#pragma unroll
+                for (int i = 0; i < RM; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < RM; ++i) {
+            const int mm = tm + 16 * i;
+            if (m0 + mm >= op.count) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t jg = j0 + tj + 16 * j;
+                if (jg >= op.J) continue;
+                T* p = C + offC[mm] + jg * op.scq;
+                *p = op.accumulate ? *p + acc[i][j] : acc[i][j];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void unit_ew(const BOp& op, int64_t e0, int64_t e1)
+{
+    const T* A = static_cast<const T*>(op.A);
+    const T* B = static_cast<const T*>(op.B);
+    T* C = static_cast<T*>(op.C);
+    const bool unary = op.eop == TL_COPY || op.eop == TL_SCALE;
+    const T alpha = (T)op.alpha;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
+        int64_t oa, ob, oc;
+        bdecode(op, e, oa, ob, oc);
+        T x = __ldg(A + oa);
+        T y = unary ? T(0) : __ldg(B + ob);
+        T r;
+        switch (op.eop) {
+        case TL_ADD: r = x + y; break;
+        case TL_SUB: r = x - y; break;
+        case TL_MUL: r = x * y; break;
+        case TL_DIV: r = x / y; break;
+        case TL_COPY: r = x; break;
+        default: r = alpha * x; break;
+        }
+        C[oc] = r;
+    }
+}
+
+template <typename T>
+__device__ void run_unit(const BOp& op, int64_t u, uint8_t* smem)
+{
+    const int64_t e0 = (u - op.ubegin) * op.unit;
+    const int64_t e1 = min(op.count, e0 + op.unit);
+    switch (op.variant) {
+    case BV_TTV_COL: unit_ttv_col<T>(op, e0, e1); break;
+    case BV_TTV_ROW4: unit_ttv_row<T, 4>(op, e0, e1); break;
+    case BV_TTV_ROW8: unit_ttv_row<T, 8>(op, e0, e1); break;
+    case BV_TTV_ROW32: unit_ttv_row<T, 32>(op, e0, e1); break;
+    case BV_TTM_32: unit_ttm<T, 32>(op, e0, smem); break;
+    case BV_TTM_64: unit_ttm<T, 64>(op, e0, smem); break;
+    default: unit_ew<T>(op, e0, e1); break;
+    }
+}
+
+constexpr size_t kSmem = 8 * 16 * (64 + 1 + 64 + 1) + 2 * 64 * 8;   // FP64 ttm tile
+
+__global__ void __launch_bounds__(kThreads) batch_kernel(const BOp* __restrict__ ops, int nops,
+                                                         int64_t total_units,
+                                                         unsigned long long* counter)
+{
+    __shared__ __align__(16) uint8_t smem[kSmem];
+    __shared__ __align__(16) BOp sop;
+    __shared__ int64_t s_unit;
+    __shared__ int s_op;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int64_t u = (int64_t)atomicAdd(counter, 1ull);
+            s_unit = u;
+            if (u < total_units) {
+                int lo = 0, hi = nops - 1;          // last op with ubegin <= u
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) / 2;
+                    if (ops[mid].ubegin <= u) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_op = lo;
+            }
+        }
+        __syncthreads();
+        const int64_t u = s_unit;
+        if (u >= total_units) break;
+        {
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(ops + s_op);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&sop);
+            for (int i = threadIdx.x; i < (int)(sizeof(BOp) / 4); i += kThreads) dst[i] = src[i];
+        }
+        __syncthreads();
+        if (sop.dtype == TL_F64) run_unit<double>(sop, u, smem);
+        else run_unit<float>(sop, u, smem);
+        __syncthreads();
+    }
+}
+
+// -------------------------------------------------------------- autotuner --
+
+struct Candidate {
+    int32_t variant;
+    int64_t unit;
+};
+
+std::string class_key(const BOp& op)
+{
+    auto lg = [](int64_t x) { int b = 0; while ((int64_t(1) << b) < x) ++b; return b; };
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "k%d|d%d|row%d|nq%d|J%d|cnt%d", op.kind, op.dtype,
+                  op.kind == TL_OP_TTV && op.saq == 1 ? 1 : 0, lg(op.nq), lg(op.J), lg(op.count));
+    return buf;
+}
+
+std::vector<Candidate> candidates(const BOp& op)
+{
+    std::vector<Candidate> c;
+    if (op.kind == TL_OP_TTV) {
+        if (op.saq == 1) {
+            for (int32_t v : {BV_TTV_ROW4, BV_TTV_ROW8, BV_TTV_ROW32})
+                for (int64_t u : {256, 1024}) c.push_back({v, u});
+        }
+        for (int64_t u : {256, 1024, 4096}) c.push_back({BV_TTV_COL, u});
+    } else if (op.kind == TL_OP_TTM) {
+        c.push_back({BV_TTM_32, 32});
+        c.push_back({BV_TTM_64, 64});
+    } else {
+        for (int64_t u : {1024, 8192}) c.push_back({BV_EW, u});
+    }
+    return c;
+}
+
+// Default choice when tuning is off.
+Candidate heuristic(const BOp& op)
+{
+    if (op.kind == TL_OP_TTV) {
+        if (op.saq == 1 && op.nq >= 32) return {BV_TTV_ROW8, 256};
+        return {BV_TTV_COL, 1024};
+    }
+    if (op.kind == TL_OP_TTM) return op.count >= 4096 ? Candidate{BV_TTM_64, 64} : Candidate{BV_TTM_32, 32};
+    return {BV_EW, 8192};
+}
+
+struct TuneCache {
+    std::mutex mu;
+    bool loaded = false;
+    std::map<std::string, Candidate> table;
+    std::string path;
+
+    void load()
+    {
+        if (loaded) return;
+        loaded = true;
+        const char* p = std::getenv("TL_TUNE_CACHE");
+        if (p && *p) {
+            path = p;
+        } else {
+            const char* h = std::getenv("HOME");
+            path = std::string(h ? h : "/tmp") + "/.cache/tlgb_tune.txt";
+        }
+        std::ifstream in(path);
+        std::string key;
+        Candidate c;
+        while (in >> key >> c.variant >> c.unit) table[key] = c;
+    }
+    void save()
+    {
+        std::string dir = path.substr(0, path.find_last_of('/'));
+        if (!dir.empty()) mkdir(dir.c_str(), 0755);   // best effort; may exist
+        std::ofstream out(path);
+        if (!out) return;
+        for (auto& kv : table) out << kv.first << ' ' << kv.second.variant << ' ' << kv.second.unit << '\n';
+    }
+};
+
+TuneCache g_tune;
+
+std::string device_tag()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "dev?";
+    std::string s = prop.name;
+    for (auto& ch : s)
+        if (ch == ' ') ch = '_';
+    return s + "_sm" + std::to_string(prop.multiProcessorCount);
+}
+
+int grid_size()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel, kThreads, 0);
+    if (per < 1) per = 1;
+    int g = per * device_sms();
+    if (dev >= 0 && dev < 64) cached[dev] = g;
+    return g;
+}
+
+int64_t units_of(const BOp& op) { return op.count == 0 ? 0 : (op.count + op.unit - 1) / op.unit; }
+
+}  // namespace
+
+// ------------------------------------------------------------ batch object --
+
+struct Batch {
+    std::vector<BOp> host;
+    BOp* dev_ops = nullptr;
+    unsigned long long* counter = nullptr;
+    int64_t total_units = 0;
+    int32_t flags = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    size_t bytes = 0;            // algorithmic bytes of all operations
+    int direct = 0;              // operations run by their own kernels
+    std::vector<tl_op> direct_ops;
+};
+
+static int fill_op(const tl_op& o, BOp& b, size_t& bytes, bool& direct)
+{
+    std::memset(&b, 0, sizeof b);
+    b.kind = o.kind;
+    b.accumulate = o.accumulate ? 1 : 0;
+    direct = false;
+    const int sms = device_sms() > 0 ? device_sms() : 152;
+    if (o.kind == TL_OP_TTV) {
+        Tensor A, C;
+        TtvPlan P;
+        int rc = prepare_ttv(&o.A, o.vec, o.incb, o.q, &o.C, sms, A, C, P);
+        if (rc) return rc;
+        if (P.out.nd > kBD) { direct = true; return TL_OK; }
+        b.dtype = A.dtype;
+        b.nd = P.out.nd;
+        for (int d = 0; d < P.out.nd; ++d) {
+            b.n[d] = P.out.d[d].n;
+            b.s0[d] = P.out.d[d].s[0];
+            b.s1[d] = P.out.d[d].s[1];
+        }
+        b.count = P.nout;
+        b.nq = P.nq;
+        b.saq = P.saq;
+        b.incb = o.incb;
+        b.A = A.data;
+        b.B = o.vec;
+        b.C = C.data;
+        bytes += (size_t)(A.count() + C.count() + P.nq) * A.elem();
+    } else if (o.kind == TL_OP_TTM) {
+        Tensor A, C;
+        TtmPlan P;
+        int rc = prepare_ttm(&o.A, o.vec, o.J, o.ldb_row, o.ldb_col, o.q, &o.C, o.precision, A, C, P);
+        if (rc) return rc;
+        if (P.rows.nd > kBD || P.kernel == K_TTM_TC) { direct = true; return TL_OK; }
+        b.dtype = A.dtype;
+        b.nd = P.rows.nd;
+        for (int d = 0; d < P.rows.nd; ++d) {
+            b.n[d] = P.rows.d[d].n;
+            b.s0[d] = P.rows.d[d].s[0];
+            b.s1[d] = P.rows.d[d].s[1];
+        }
+        b.count = P.M;
+        b.nq = P.nq;
+        b.saq = P.saq;
+        b.J = P.J;
+        b.scq = P.scq;
+        b.ldb_row = P.ldb_row;
+        b.ldb_col = P.ldb_col;
+        b.A = A.data;
+        b.B = o.vec;
+        b.C = C.data;
+        bytes += (size_t)(A.count() + C.count() + P.J * P.nq) * A.elem();
+    } else if (o.kind == TL_OP_ENTRYWISE) {
+        Tensor A, B, C;
+        EwPlan P;
+        bool hasB = false;
+        bool unary = o.entry_op == TL_COPY || o.entry_op == TL_SCALE;
+        int rc = prepare_entrywise(o.entry_op, &o.A, unary ? nullptr : &o.B, &o.C, A, B, C, hasB, P);
+        if (rc) return rc;
+        if (P.sp.nd > kBD) { direct = true; return TL_OK; }
+        b.dtype = A.dtype;
+        b.nd = P.sp.nd;
+        for (int d = 0; d < P.sp.nd; ++d) {
+            b.n[d] = P.sp.d[d].n;
+            b.s0[d] = P.sp.d[d].s[0];
+            b.s1[d] = P.sp.d[d].s[1];
+            b.s2[d] = P.sp.d[d].s[2];
+        }
+        b.count = P.N;
+        b.eop = o.entry_op;
+        b.alpha = o.alpha;
+        b.A = A.data;
+        b.B = hasB ? B.data : A.data;
+        b.C = C.data;
+        bytes += (size_t)((hasB ? 3 : 2) * A.count()) * A.elem();
+    } else {
+        return TL_EINVAL;
+    }
+    return TL_OK;
+}
+
+// Times one candidate on a one-operation table (milliseconds, best of 3).
+static float time_candidate(const BOp& op, Candidate c, BOp* dev_one, unsigned long long* counter,
+                            cudaStream_t st)
+{
+    BOp t = op;
+    t.variant = c.variant;
+    t.unit = c.unit;
+    t.ubegin = 0;
+    const int64_t units = units_of(t);
+    cudaMemcpyAsync(dev_one, &t, sizeof t, cudaMemcpyHostToDevice, st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    const int grid = grid_size();
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+        cudaEventRecord(e0, st);
+        batch_kernel<<<grid, kThreads, 0, st>>>(dev_one, 1, units, counter);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+int batch_create(const tl_op* ops, size_t count, int32_t flags, void* stream, Batch** out)
+{
+    if (!out || (!ops && count)) return TL_EINVAL;
+    *out = nullptr;
+    Batch* B = new Batch();
+    B->flags = flags;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (size_t i = 0; i < count; ++i) {
+        BOp b;
+        bool direct = false;
+        int rc = fill_op(ops[i], b, B->bytes, direct);
+        if (rc) {
+            delete B;
+            return rc;
+        }
+        if (direct) {
+            B->direct_ops.push_back(ops[i]);
+            B->direct++;
+            continue;
+        }
+        if (b.count > 0) B->host.push_back(b);
+    }
+    // variant and unit size per operation
+    std::map<std::string, Candidate> chosen;
+    if (flags & TL_BATCH_TUNE) {
+        std::lock_guard<std::mutex> lk(g_tune.mu);
+        g_tune.load();
+        const std::string tag = device_tag();
+        // representative = largest operation of each class
+        std::map<std::string, const BOp*> rep;
+        for (const BOp& b : B->host) {
+            std::string k = tag + "|" + class_key(b);
+            auto it = rep.find(k);
+            if (it == rep.end() || it->second->count < b.count) rep[k] = &b;
+        }
+        BOp* dev_one = nullptr;
+        unsigned long long* ctr = nullptr;
+        bool tuned = false;
+        for (auto& kv : rep) {
+            auto hit = g_tune.table.find(kv.first);
+            if (hit != g_tune.table.end()) {
+                chosen[kv.first] = hit->second;
+                continue;
+            }
+            if (!dev_one) {
+                if (cudaMalloc(&dev_one, sizeof(BOp)) != cudaSuccess ||
+                    cudaMalloc(&ctr, sizeof(unsigned long long)) != cudaSuccess) {
+                    cudaGetLastError();
+                    break;
+                }
+            }
+            Candidate best = heuristic(*kv.second);
+            float best_ms = 1e30f;
+            for (Candidate c : candidates(*kv.second)) {
+                float ms = time_candidate(*kv.second, c, dev_one, ctr, st);
+                if (ms < best_ms) { best_ms = ms; best = c; }
+            }
+            chosen[kv.first] = best;
+            g_tune.table[kv.first] = best;
+            tuned = true;
+        }
+        if (dev_one) cudaFree(dev_one);
+        if (ctr) cudaFree(ctr);
+        if (tuned) g_tune.save();
+        for (BOp& b : B->host) {
+            auto it = chosen.find(tag + "|" + class_key(b));
+            Candidate c = it != chosen.end() ? it->second : heuristic(b);
+            b.variant = c.variant;
+            b.unit = c.unit;
+        }
+    } else {
+        for (BOp& b : B->host) {
+            Candidate c = heuristic(b);
+            b.variant = c.variant;
+            b.unit = c.unit;
+        }
+    }
+    // large operations first, so the tail of the persistent launch is small units
+    std::stable_sort(B->host.begin(), B->host.end(),
+                     [](const BOp& x, const BOp& y) { return x.count * (x.kind == TL_OP_TTM ? x.J : 1) >
+                                                             y.count * (y.kind == TL_OP_TTM ? y.J : 1); });
+    int64_t u = 0;
+    for (BOp& b : B->host) {
+        b.ubegin = u;
+        u += units_of(b);
+    }
+    B->total_units = u;
+    if (!B->host.empty()) {
+        if (cudaMalloc(&B->dev_ops, sizeof(BOp) * B->host.size()) != cudaSuccess ||
+            cudaMalloc(&B->counter, sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            batch_destroy(B);
+            return TL_ENOMEM;
+        }
+        if (cudaMemcpyAsync(B->dev_ops, B->host.data(), sizeof(BOp) * B->host.size(),
+                            cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            batch_destroy(B);
+            return TL_ECUDA;
+        }
+    }
+    *out = B;
+    return TL_OK;
+}
+
+static int enqueue(Batch* B, cudaStream_t st)
+{
+    if (B->total_units > 0) {
+        if (cudaMemsetAsync(B->counter, 0, sizeof(unsigned long long), st) != cudaSuccess) return TL_ECUDA;
+        batch_kernel<<<grid_size(), kThreads, 0, st>>>(B->dev_ops, (int)B->host.size(),
+                                                       B->total_units, B->counter);
+        if (cudaPeekAtLastError() != cudaSuccess) return TL_ECUDA;
+    }
+    return TL_OK;
+}
+
+int batch_run(Batch* B, void* stream)
+{
+    if (!B) return TL_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // operations the batch kernel does not take run through their own kernels
+    for (const tl_op& o : B->direct_ops) {
+        int rc = TL_OK;
+        if (o.kind == TL_OP_TTV) rc = tl_ttv(&o.A, o.vec, o.incb, o.q, &o.C, o.accumulate, stream);
+        else if (o.kind == TL_OP_TTM)
+            rc = tl_ttm(&o.A, o.vec, o.J, o.ldb_row, o.ldb_col, o.q, &o.C, o.precision, o.accumulate, stream);
+        else
+            rc = tl_entrywise(o.entry_op, &o.A,
+                              (o.entry_op == TL_COPY || o.entry_op == TL_SCALE) ? nullptr : &o.B,
+                              o.alpha, &o.C, stream);
+        if (rc) return rc;
+    }
+    if (B->total_units == 0) return TL_OK;
+    if (!(B->flags & TL_BATCH_GRAPH)) {
+        int rc = enqueue(B, st);
+        if (rc == TL_OK) count_launches(1);
+        return rc;
+    }
+    if (!B->exec || B->graph_stream != st) {
+        if (B->exec) cudaGraphExecDestroy(B->exec);
+        if (B->graph) cudaGraphDestroy(B->graph);
+        B->exec = nullptr;
+        B->graph = nullptr;
+        // capture on a private stream, then launch the graph on the caller's
+        cudaStream_t cap;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return TL_ECUDA;
+        cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        int rc = enqueue(B, cap);
+        cudaError_t e = cudaStreamEndCapture(cap, &B->graph);
+        cudaStreamDestroy(cap);
+        if (rc || e != cudaSuccess) return TL_ECUDA;
+        if (cudaGraphInstantiate(&B->exec, B->graph, 0) != cudaSuccess) return TL_ECUDA;
+        B->graph_stream = st;
+    }
+    if (cudaGraphLaunch(B->exec, st) != cudaSuccess) return TL_ECUDA;
+    count_launches(1);
+    return TL_OK;
+}
+
+int batch_destroy(Batch* B)
+{
+    if (!B) return TL_OK;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->dev_ops) cudaFree(B->dev_ops);
+    if (B->counter) cudaFree(B->counter);
+    delete B;
+    return TL_OK;
+}
+
+size_t batch_bytes(const Batch* B) { return B ? B->bytes : 0; }
+
+int batch_set_variant(Batch* B, int32_t kind, int32_t variant, int64_t unit, void* stream)
+{
+    if (!B || unit < 1) return TL_EINVAL;
+    const bool ok_kind =
+        (kind == TL_OP_TTV && (variant == BV_TTV_COL || variant == BV_TTV_ROW4 ||
+                               variant == BV_TTV_ROW8 || variant == BV_TTV_ROW32)) ||
+        (kind == TL_OP_TTM && (variant == BV_TTM_32 || variant == BV_TTM_64)) ||
+        (kind == TL_OP_ENTRYWISE && variant == BV_EW);
+    if (!ok_kind) return TL_EINVAL;
+    if (kind == TL_OP_TTM) unit = variant == BV_TTM_32 ? 32 : 64;   // a ttm unit is one row tile
+    for (BOp& b : B->host)
+        if (b.kind == kind) {
+            b.variant = variant;
+            b.unit = unit;
+        }
+    int64_t u = 0;
+    for (BOp& b : B->host) {
+        b.ubegin = u;
+        u += units_of(b);
+    }
+    B->total_units = u;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    B->exec = nullptr;
+    B->graph = nullptr;
+    if (B->host.empty()) return TL_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(B->dev_ops, B->host.data(), sizeof(BOp) * B->host.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return TL_ECUDA;
+    return TL_OK;
+}
+
+int batch_describe(const Batch* B, char* buf, size_t len)
+{
+    if (!B || !buf || !len) return TL_EINVAL;
+    int hist[8] = {0};
+    for (const BOp& b : B->host) hist[b.variant & 7]++;
+    std::snprintf(buf, len,
+                  "{\"ops\":%zu,\"direct\":%d,\"units\":%lld,\"grid\":%d,\"bytes\":%zu,"
+                  "\"variants\":{\"ttv_col\":%d,\"ttv_row4\":%d,\"ttv_row8\":%d,\"ttv_row32\":%d,"
+                  "\"ttm32\":%d,\"ttm64\":%d,\"ew\":%d}}",
+                  B->host.size(), B->direct, (long long)B->total_units, grid_size(), B->bytes,
+                  hist[0], hist[1], hist[2], hist[3], hist[4], hist[5], hist[6]);
+    return TL_OK;
+}
+
+// ------------------------------------------------------------------ slots --
+
+struct Slot {
+    size_t cap = 0;
+    BOp* dev = nullptr;
+    BOp* pinned = nullptr;
+    unsigned long long* counter = nullptr;
+};
+
+Slot* slot_create(size_t capacity)
+{
+    Slot* s = new Slot();
+    s->cap = capacity;
+    if (cudaMalloc(&s->dev, sizeof(BOp) * capacity) != cudaSuccess ||
+        cudaMallocHost(&s->pinned, sizeof(BOp) * capacity) != cudaSuccess ||
+        cudaMalloc(&s->counter, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        slot_destroy(s);
+        return nullptr;
+    }
+    return s;
+}
+
+void slot_destroy(Slot* s)
+{
+    if (!s) return;
+    if (s->dev) cudaFree(s->dev);
+    if (s->pinned) cudaFreeHost(s->pinned);
+    if (s->counter) cudaFree(s->counter);
+    delete s;
+}
+
+int slot_launch(Slot* s, const tl_op* const* ops, size_t n, cudaStream_t st)
+{
+    size_t m = 0, bytes = 0;
+    int64_t units = 0;
+    int rc = TL_OK;
+    for (size_t i = 0; i < n && rc == TL_OK; ++i) {
+        BOp b;
+        bool direct = false;
+        rc = fill_op(*ops[i], b, bytes, direct);
+        if (rc) break;
+        if (direct || !s || m == s->cap) {
+            const tl_op& o = *ops[i];
+            if (o.kind == TL_OP_TTV) rc = tl_ttv(&o.A, o.vec, o.incb, o.q, &o.C, o.accumulate, st);
+            else if (o.kind == TL_OP_TTM)
+                rc = tl_ttm(&o.A, o.vec, o.J, o.ldb_row, o.ldb_col, o.q, &o.C, o.precision,
+                            o.accumulate, st);
+            else
+                rc = tl_entrywise(o.entry_op, &o.A,
+                                  (o.entry_op == TL_COPY || o.entry_op == TL_SCALE) ? nullptr : &o.B,
+                                  o.alpha, &o.C, st);
+            continue;
+        }
+        if (b.count == 0) continue;
+        Candidate c = heuristic(b);
+        {
+            std::lock_guard<std::mutex> lk(g_tune.mu);
+            if (g_tune.loaded) {
+                auto it = g_tune.table.find(device_tag() + "|" + class_key(b));
+                if (it != g_tune.table.end()) c = it->second;
+            }
+        }
+        b.variant = c.variant;
+        b.unit = c.unit;
+        b.ubegin = units;
+        units += units_of(b);
+        s->pinned[m++] = b;
+    }
+    if (rc) return rc;
+    if (m == 0 || !s) return TL_OK;
+    if (cudaMemcpyAsync(s->dev, s->pinned, sizeof(BOp) * m, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(s->counter, 0, sizeof(unsigned long long), st) != cudaSuccess)
+        return TL_ECUDA;
+    batch_kernel<<<grid_size(), kThreads, 0, st>>>(s->dev, (int)m, units, s->counter);
+    if (cudaPeekAtLastError() != cudaSuccess) return TL_ECUDA;
+    count_launches(1);
+    return TL_OK;
+}
+
+long long op_bytes(const tl_op& o)
+{
+    BOp b;
+    size_t bytes = 0;
+    bool direct = false;
+    int rc = fill_op(o, b, bytes, direct);
+    return rc ? (long long)rc : (long long)bytes;
+}
+
+}  // namespace tl
+
+using namespace tl;
+
+extern "C" {
+
+int tl_batch_create(const tl_op* ops, size_t count, int32_t flags, void* stream, tl_batch** out)
+{
+    return batch_create(ops, count, flags, stream, reinterpret_cast<Batch**>(out));
+}
+
+int tl_batch_run(tl_batch* b, void* stream) { return batch_run(reinterpret_cast<Batch*>(b), stream); }
+
+int tl_batch_destroy(tl_batch* b) { return batch_destroy(reinterpret_cast<Batch*>(b)); }
+
+int tl_batch_set_variant(tl_batch* b, int32_t kind, int32_t variant, int64_t unit, void* stream)
+{
+    return batch_set_variant(reinterpret_cast<Batch*>(b), kind, variant, unit, stream);
+}
+
+int tl_batch_describe(const tl_batch* b, char* buf, size_t len)
+{
+    return batch_describe(reinterpret_cast<const Batch*>(b), buf, len);
+}
+
+}  // extern "C"

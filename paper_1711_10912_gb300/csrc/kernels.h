@@ -36,4 +36,6 @@ int ttm_tc_launches(const TtmPlan& P);
 // TL_ETIMEOUT if a bounded wait in a tensor-core kernel gave up since the
 // last cleared check, else TL_OK (reads the device status word).
 int ttm_tc_status(bool clear);
+// Launches the bounded-wait self test (see tl_selftest_wait_timeout).
+int selftest_wait_timeout(double limit_us, cudaStream_t st);
 }  // namespace tl

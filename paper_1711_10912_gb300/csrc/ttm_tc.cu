@@ -89,18 +89,33 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: false (and the status word set) after kTimeoutCycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// Bounded wait: false (and the status word set) after `limit` SM cycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long limit = kTimeoutCycles)
 {
     if (mbar_try(bar, parity)) return true;
     long long t0 = clock64();
     while (!mbar_try(bar, parity)) {
-        if (clock64() - t0 > kTimeoutCycles) {
+        if (clock64() - t0 > limit) {
             atomicOr(&g_tc_status, 1u);
             return false;
         }
     }
     return true;
+}
+
+// One thread waits on a barrier whose phase never completes (its arrival
+// count is 2 and only one arrival happens); the bounded wait gives up.
+__global__ void selftest_wait_kernel(long long limit)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        const uint32_t b = smem_u32(&bar);
+        mbar_init(b, 2);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_arrive(b);
+        mbar_wait(b, 0u, limit);
+    }
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
@@ -750,6 +765,17 @@ int launch_ttm_tc(const TtmPlan& P, const void* A, const void* B, void* C, int a
     case TL_P_BF16X3: return launch_prec<TL_P_BF16X3>(P, A, B, C, accumulate, num_sms, st);
     default: return TL_EUNSUPPORTED;
     }
+}
+
+int selftest_wait_timeout(double limit_us, cudaStream_t st)
+{
+    if (!(limit_us > 0) || limit_us > 1e6) return TL_EINVAL;
+    int dev = 0, khz = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0) khz = 2000000;
+    const long long cycles = (long long)(limit_us * 1e-3 * khz);
+    selftest_wait_kernel<<<1, 32, 0, st>>>(cycles);
+    return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
 }
 
 int ttm_tc_status(bool clear)
