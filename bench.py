@@ -60,6 +60,12 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 19,
                     help="outputs per ttv/ttm op in the CPU-oracle sample")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--batch-ops", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=3000)
+    ap.add_argument("--serve-rates", default="2000,10000,40000")
     return ap.parse_args()
 
 
@@ -70,6 +76,24 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(torch, value: float, device=None) -> float:
+    """Largest value over all ranks (the value itself in a single process).
+    Timings are reduced this way, so a step counts as long as its slowest rank."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(bytes_per_rank_step: float, world: int, steps: int, elapsed_ms: float) -> float:
+    """Whole-job GB/s: every rank processes its own replica of the workload
+    (weak scaling), so the job moves world x steps x bytes in the slowest
+    rank's time."""
+    return bytes_per_rank_step * world * steps / (elapsed_ms / 1e3) / 1e9
 
 
 def load_peaks():
@@ -410,13 +434,9 @@ def main():
     barrier()
     launches = tl.tl_launch_count() - launches0
     clocks = sampler.stop()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(torch, t_start.elapsed_time(t_end), dev)
     ms_per_step = elapsed_ms / args.steps
-    value = wl.step_bytes * world * args.steps / (elapsed_ms / 1e3) / 1e9
+    value = job_throughput(wl.step_bytes, world, args.steps, elapsed_ms)
 
     # per-call durations and the dominant kernel
     per_call = [[evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(args.steps)]
@@ -467,6 +487,22 @@ def main():
     if not args.no_e2e:
         e2e = measure_e2e(tl, torch, wl, args, sh, world, barrier)
 
+    extras = {}
+    step_bytes, step_flops = wl.step_bytes, wl.step_flops
+    if world == 1:
+        del wl
+        torch.cuda.empty_cache()
+        if not args.no_batch:
+            extras["batch"] = measure_batch(tl, torch, dev, sh, args.batch_ops)
+            torch.cuda.empty_cache()
+        if not args.no_serve:
+            rates = [float(x) for x in args.serve_rates.split(",") if x]
+            extras["serve"] = measure_serve(tl, torch, dev, sh, args.serve_requests, rates)
+            torch.cuda.empty_cache()
+        if not args.no_precision:
+            extras["precision"] = measure_precision(tl, torch, dev, sh)
+            torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(case, edge, args.cpu_sample)
@@ -480,14 +516,293 @@ def main():
                            "ttm_precision": TTM_PRECISION_NAME.get(args.ttm_precision),
                            "l2": "inputs larger than L2 (1 GiB per tensor); no flush",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "step_gbytes": wl.step_bytes / 1e9, "step_gflops": wl.step_flops / 1e9,
+                "step_gbytes": step_bytes / 1e9, "step_gflops": step_flops / 1e9,
                 "roofline": roof, "breakdown": breakdown, "per_call": per_op_q,
                 "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu}
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+# ------------------------------------------------------------- batching ---
+
+def _op_for_unit(tl, torch, dev, u, seed, keep):
+    """Device buffers and a tl_op for one batch unit (FP32)."""
+    import synth
+    n, pi, q = u.n, u.pi, u.q
+    N = int(np.prod(n))
+    A = synth.device_normal(torch, N, seed, torch.float32, dev)
+    DA = tl.Desc(A, n, pi)
+    if u.op == "ttv":
+        nout = tuple(x for r, x in enumerate(n) if r != q - 1)
+        pic = tuple(sorted(r for r in pi if r != q).index(r) + 1 for r in pi if r != q)
+        b = synth.device_normal(torch, n[q - 1], seed + 1, torch.float32, dev)
+        C = torch.empty(N // n[q - 1], dtype=torch.float32, device=dev)
+        DC = tl.Desc(C, nout, pic)
+        op = tl.make_op(tl.TL_OP_TTV, DA, DC, q=q, vec=b)
+        byts = (N + N // n[q - 1] + n[q - 1]) * 4
+        flops = 2 * N
+        keep += [A, b, C, DA, DC]
+        call = (tl.tl_ttv, (DA, b, 1, q, DC, 0))
+    else:
+        J = u.J
+        nout = tuple(J if r == q - 1 else x for r, x in enumerate(n))
+        B = synth.device_normal(torch, J * n[q - 1], seed + 2, torch.float32, dev)
+        C = torch.empty(N // n[q - 1] * J, dtype=torch.float32, device=dev)
+        DC = tl.Desc(C, nout, pi)
+        op = tl.make_op(tl.TL_OP_TTM, DA, DC, q=q, vec=B, J=J, ldb_row=n[q - 1], ldb_col=1)
+        byts = (N + N // n[q - 1] * J + J * n[q - 1]) * 4
+        flops = 2 * N * J
+        keep += [A, B, C, DA, DC]
+        call = (tl.tl_ttm, (DA, B, J, n[q - 1], 1, q, DC, tl.TL_P_DEFAULT, 0))
+    return op, call, byts, flops, C
+
+
+def measure_batch(tl, torch, dev, sh, nops, reps=5):
+    """4096 FP32 ttv/ttm of order 3-6 with random extents and layouts: a plain
+    loop of per-call launches against one persistent, graph-captured launch
+    with autotuned units."""
+    import synth
+    units = synth.batch_units(nops)
+    keep, ops, calls, outs = [], [], [], []
+    tot_b, tot_f = 0, 0
+    for i, u in enumerate(units):
+        op, call, b, f, C = _op_for_unit(tl, torch, dev, u, 10_000 + 7 * i, keep)
+        ops.append(op)
+        calls.append(call)
+        outs.append(C)
+        tot_b += b
+        tot_f += f
+    torch.cuda.synchronize()
+
+    def plain():
+        for fn, args in calls:
+            tl.check(fn(*args, sh))
+
+    rc, batch = tl.tl_batch_create(ops, tl.TL_BATCH_TUNE | tl.TL_BATCH_GRAPH, sh)
+    tl.check(rc, "tl_batch_create")
+    info = json.loads(tl.tl_batch_describe(batch)[1])
+
+    def persistent():
+        tl.check(tl.tl_batch_run(batch, sh))
+
+    res = {}
+    for name, fn in (("plain", plain), ("persistent_graph", persistent)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / reps
+        dev_ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms_per_batch": round(dev_ms, 3), "host_ms_per_batch": round(wall * 1e3, 3),
+                     "ops/s": round(nops / (dev_ms / 1e3), 1),
+                     "GB/s": round(tot_b / (dev_ms / 1e3) / 1e9, 1),
+                     "TFLOP/s": round(tot_f / (dev_ms / 1e3) / 1e12, 3)}
+    # the persistent results equal the per-call results within FP32 tolerance
+    ref = [o.clone() for o in outs]
+    persistent()
+    torch.cuda.synchronize()
+    plain()
+    torch.cuda.synchronize()
+    worst = 0.0
+    for a, b in zip(ref, outs):
+        d = float(torch.linalg.vector_norm((a - b).double()))
+        nrm = float(torch.linalg.vector_norm(b.double()))
+        worst = max(worst, d / nrm if nrm > 0 else d)
+    tl.tl_batch_destroy(batch)
+    res["ops"] = nops
+    res["gbytes"] = tot_b / 1e9
+    res["speedup"] = round(res["plain"]["ms_per_batch"] / res["persistent_graph"]["ms_per_batch"], 2)
+    res["max_rel_diff_vs_plain"] = worst
+    res["plan"] = info
+    return res
+
+
+# -------------------------------------------------------------- serving ---
+
+def measure_serve(tl, torch, dev, sh, nreq, rates, pool=192, budget=40_000_000_000):
+    """Poisson stream of ttv / ttm / entrywise requests (order 2-7, lognormal
+    element counts over 1e3-1e8, 20% FP64) on device-resident operands:
+    continuous batching against serving one request at a time."""
+    import synth
+    reqs = synth.serving_stream(pool, 1.0, seed=synth.BASE_SEED + 5)
+    keep, ops, calls, sizes = [], [], [], []
+    for i, r in enumerate(reqs):
+        dt = torch.float64 if r.dtype == "f64" else torch.float32
+        es = 8 if r.dtype == "f64" else 4
+        n, pi, q = r.n, r.pi, r.q
+        N = int(np.prod(n))
+        A = synth.device_normal(torch, N, 20_000 + i, dt, dev)
+        DA = tl.Desc(A, n, pi)
+        if r.op == "ttv":
+            nout = tuple(x for k, x in enumerate(n) if k != q - 1)
+            pic = tuple(sorted(k for k in pi if k != q).index(k) + 1 for k in pi if k != q)
+            b = synth.device_normal(torch, n[q - 1], 30_000 + i, dt, dev)
+            C = torch.empty(N // n[q - 1], dtype=dt, device=dev)
+            DC = tl.Desc(C, nout, pic)
+            ops.append(tl.make_op(tl.TL_OP_TTV, DA, DC, q=q, vec=b))
+            calls.append((tl.tl_ttv, (DA, b, 1, q, DC, 0)))
+            sizes.append((N + N // n[q - 1]) * es)
+            keep += [A, b, C, DA, DC]
+        elif r.op == "ttm":
+            J = r.J
+            nout = tuple(J if k == q - 1 else x for k, x in enumerate(n))
+            B = synth.device_normal(torch, J * n[q - 1], 30_000 + i, dt, dev)
+            C = torch.empty(N // n[q - 1] * J, dtype=dt, device=dev)
+            DC = tl.Desc(C, nout, pi)
+            prec = tl.TL_P_BF16X3 if r.dtype == "f32" else tl.TL_P_F64
+            ops.append(tl.make_op(tl.TL_OP_TTM, DA, DC, q=q, vec=B, J=J, ldb_row=n[q - 1],
+                                  ldb_col=1, precision=prec))
+            calls.append((tl.tl_ttm, (DA, B, J, n[q - 1], 1, q, DC, prec, 0)))
+            sizes.append((N + N // n[q - 1] * J) * es)
+            keep += [A, B, C, DA, DC]
+        else:
+            Bt = synth.device_normal(torch, N, 30_000 + i, dt, dev)
+            C = torch.empty(N, dtype=dt, device=dev)
+            DB, DC = tl.Desc(Bt, n, r.pi_b), tl.Desc(C, n, r.pi_c)
+            ops.append(tl.make_op(tl.TL_OP_ENTRYWISE, DA, DC, B=DB, entry_op=tl.TL_ADD))
+            calls.append((tl.tl_entrywise, (tl.TL_ADD, DA, DB, 1.0, DC)))
+            sizes.append(3 * N * es)
+            keep += [A, Bt, C, DA, DB, DC]
+    torch.cuda.synchronize()
+    # warm every call once (plans, workspaces)
+    for fn, args in calls:
+        tl.check(fn(*args, sh))
+    torch.cuda.synchronize()
+
+    def pct(x, p):
+        return float(np.percentile(np.asarray(x), p)) if x else None
+
+    out = {"pool_requests": pool, "requests_per_rate": nreq, "budget_bytes": budget, "rates": []}
+    for rate in rates:
+        g = synth.rng(int(rate))
+        pick = g.integers(0, pool, size=nreq)
+        arr = np.cumsum(g.exponential(1.0 / rate, size=nreq))
+        # ---- continuous batching server
+        rc, ctx = tl.tl_ctx_create(budget, 4, tl.TL_CTX_PERSISTENT)
+        tl.check(rc, "tl_ctx_create")
+        tickets, sub_lag = [], []
+        t0 = time.perf_counter()
+        for i in range(nreq):
+            now = time.perf_counter() - t0
+            if arr[i] > now:
+                time.sleep(arr[i] - now)
+            lag = time.perf_counter() - t0 - arr[i]
+            rc, t = tl.tl_batch_submit(ctx, [ops[pick[i]]])
+            tl.check(rc, "tl_batch_submit")
+            tickets.append(t)
+            sub_lag.append(lag)
+        lat = []
+        for t, lag in zip(tickets, sub_lag):
+            rc, st, ms = tl.tl_wait(ctx, t, 120000.0)
+            tl.check(rc, "tl_wait")
+            lat.append(ms + lag * 1e3)
+        t_end = time.perf_counter() - t0
+        rc, maxin, batches, completed = tl.tl_ctx_stats(ctx)
+        tl.tl_ctx_destroy(ctx)
+        served = {"ops/s": round(nreq / t_end, 1), "p50_ms": round(pct(lat, 50), 3),
+                  "p99_ms": round(pct(lat, 99), 3), "batches": batches,
+                  "max_inflight_GB": round(maxin / 1e9, 3)}
+        # ---- plain: one request at a time, synchronously, on one stream
+        lat_p = []
+        t0 = time.perf_counter()
+        for i in range(nreq):
+            now = time.perf_counter() - t0
+            if arr[i] > now:
+                time.sleep(arr[i] - now)
+            fn, args = calls[pick[i]]
+            tl.check(fn(*args, sh))
+            torch.cuda.current_stream(dev).synchronize()
+            lat_p.append((time.perf_counter() - t0 - arr[i]) * 1e3)
+        t_end_p = time.perf_counter() - t0
+        plain = {"ops/s": round(nreq / t_end_p, 1), "p50_ms": round(pct(lat_p, 50), 3),
+                 "p99_ms": round(pct(lat_p, 99), 3)}
+        out["rates"].append({"offered_ops/s": rate, "served": served, "plain": plain})
+    return out
+
+
+# ------------------------------------------------------------ precision ---
+
+def measure_precision(tl, torch, dev, sh, edge=512, rank=64, samples=3000):
+    """512^3 FP32 with mode-3 slices scaled by 10^U(-3,3): ttm by a 512x512
+    and a truncated 64x512 matrix in BF16, TF32 and split-BF16x3, and the
+    all-modes Tucker projection to 64^3; errors against the FP64 oracle on
+    sampled outputs (relative Frobenius over the sample and worst relative
+    error per mode-3 slice)."""
+    import oracle
+    import synth
+    n, mem, Bfull, Bt, U = synth.precision_case(edge=edge, rank=rank)
+    A = torch.from_numpy(mem).to(dev)
+    w = oracle.strides(n)
+    res = {"shape": list(n), "cases": []}
+    g = synth.rng(4242)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, Bm in (("x512", Bfull), ("x64", Bt)):
+        J = Bm.shape[0]
+        Bd = torch.from_numpy(np.ascontiguousarray(Bm).reshape(-1)).to(dev)
+        for q in (1, 3):
+            nout = tuple(J if r == q - 1 else x for r, x in enumerate(n))
+            C = torch.empty(int(np.prod(nout)), dtype=torch.float32, device=dev)
+            idx = np.stack([g.integers(0, x, size=samples) for x in nout], axis=1)
+            ref = oracle.ttm_at(mem, n, w, q, Bm.reshape(-1), edge, 1, idx)
+            for prec in (tl.TL_P_BF16, tl.TL_P_TF32, tl.TL_P_BF16X3, tl.TL_P_F32):
+                args = (tl.Desc(A, n), Bd, J, edge, 1, q, tl.Desc(C, nout), prec, 0, sh)
+                tl.check(tl.tl_ttm(*args))
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(3):
+                    tl.tl_ttm(*args)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / 3
+                got = synth.from_memory(C.cpu().numpy(), nout, synth.first_order(3))[tuple(idx.T)]
+                rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
+                slice_worst = {}
+                for k3, r in zip(idx[:, 2], rel):
+                    slice_worst[k3] = max(slice_worst.get(k3, 0.0), float(r))
+                flops = 2 * int(np.prod(n)) * J
+                res["cases"].append({
+                    "matrix": name, "q": q, "precision": TTM_PRECISION_NAME[prec],
+                    "ms": round(ms, 4), "TFLOP/s": round(flops / (ms / 1e3) / 1e12, 2),
+                    "rel_frob_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                    "worst_slice_max_rel_err": max(slice_worst.values())})
+    # Tucker projection to rank^3: each step checked against the oracle
+    # applied to the previous step's device result
+    cur, cur_n, cur_mem = A, n, mem
+    steps = []
+    Ud = [torch.from_numpy(np.ascontiguousarray(u).reshape(-1)).to(dev) for u in U]
+    t_ms = 0.0
+    for q in (1, 2, 3):
+        nout = tuple(rank if r == q - 1 else x for r, x in enumerate(cur_n))
+        C = torch.empty(int(np.prod(nout)), dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
+        e0.record()
+        tl.check(tl.tl_ttm(tl.Desc(cur, cur_n), Ud[q - 1], rank, edge, 1, q, tl.Desc(C, nout),
+                           tl.TL_P_BF16X3, 0, sh))
+        e1.record()
+        torch.cuda.synchronize()
+        t_ms += e0.elapsed_time(e1)
+        idx = np.stack([g.integers(0, x, size=samples) for x in nout], axis=1)
+        ref = oracle.ttm_at(cur_mem, cur_n, oracle.strides(cur_n), q, U[q - 1].reshape(-1), edge,
+                            1, idx)
+        out_mem = C.cpu().numpy()
+        got = synth.from_memory(out_mem, nout, synth.first_order(3))[tuple(idx.T)]
+        steps.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        cur, cur_n, cur_mem = C, nout, out_mem
+    tucker_flops = 2 * rank * edge ** 3 + 2 * rank * rank * edge ** 2 + 2 * rank ** 3 * edge
+    res["tucker"] = {"precision": "bf16x3", "ms": round(t_ms, 3),
+                     "TFLOP/s": round(tucker_flops / (t_ms / 1e3) / 1e12, 2),
+                     "step_rel_frob_err": steps}
+    return res
 
 
 def measure_e2e(tl, torch, wl, args, sh, world, barrier):
@@ -532,12 +847,8 @@ def measure_e2e(tl, torch, wl, args, sh, world, barrier):
         step()
     e.record()
     torch.cuda.synchronize()
-    ms = s.elapsed_time(e)
-    if world > 1:
-        t = torch.tensor([ms], device=wl.dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    return {"value": round(wl.step_bytes * world * steps / (ms / 1e3) / 1e9, 2), "unit": "GB/s",
+    ms = max_over_ranks(torch, s.elapsed_time(e), wl.dev)
+    return {"value": round(job_throughput(wl.step_bytes, world, steps, ms), 2), "unit": "GB/s",
             "ms_per_step": round(ms / steps, 3), "steps": steps,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
