@@ -193,7 +193,10 @@ int tl_selftest_wait_timeout(double limit_us, void* stream)
 int tl_device_status(void* stream)
 {
     if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return TL_ECUDA;
-    return ttm_tc_status(true);
+    int a = ttm_tc_status(true);
+    int b = ttv_status(true);
+    if (a == TL_ECUDA || b == TL_ECUDA) return TL_ECUDA;
+    return (a == TL_ETIMEOUT || b == TL_ETIMEOUT) ? TL_ETIMEOUT : TL_OK;
 }
 
 const char* tl_strerror(int code)

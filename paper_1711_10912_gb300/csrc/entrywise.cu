@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) ew_tile_kernel(const EwArgs a, int64
 // hand-off.  Chosen by the planner when extents and strides allow 16-byte
 // vectors for all three operands.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) ew_tile_vec_kernel(const EwArgs a, int64_t tiles0,
+__global__ void __launch_bounds__(kThreads, 4) ew_tile_vec_kernel(const EwArgs a, int64_t tiles0,
                                                                int64_t tiles1, int64_t batch)
 {
     constexpr int VEC = 16 / sizeof(T);

@@ -8,6 +8,8 @@
 namespace tl {
 
 size_t ttv_workspace_bytes(const TtvPlan& P);
+// TL_ETIMEOUT if a bounded wait of a pipelined ttv kernel gave up (see ttm_tc_status).
+int ttv_status(bool clear);
 int launch_ttv(const TtvPlan& P, const void* A, const void* b, void* C, void* ws,
                int accumulate, int num_sms, cudaStream_t st);
 

@@ -18,12 +18,16 @@
 // streamed per k stage with bulk copies.  Split-BF16x3 issues
 // hi*hi + hi*lo + lo*hi; every product accumulates in FP32 in TMEM.
 //
-// Warp roles (320 threads, one CTA per SM, persistent over tiles):
-//   warp 0      TMA producer (one thread)
-//   warp 1      TMEM allocator and MMA issuer (one thread)
-//   warps 2-5   converters
-//   warps 6-9   epilogue: TMEM -> registers -> C (each warp owns the TMEM
-//               lane quarter warp % 4)
+// Warp roles (576 threads, one CTA per SM, persistent over tiles):
+//   warp 0       TMA producer (one thread)
+//   warp 1       TMEM allocator and MMA issuer (one thread)
+//   warps 2-9    converters: two threads per operand row, each converting
+//                half of the stage's 32 k values
+//   warps 10-17  epilogue: TMEM -> registers -> C; warp w reads the TMEM
+//                lane quarter w % 4 and every other 32-column chunk
+// Eight + eight warps rather than four + four: the conversion and drain
+// chains are latency-bound, and more warps in flight keep the HBM stream
+// busy (measured on GB300).
 // Every mbarrier wait is bounded: after about a second without progress the
 // thread records a timeout in a status word, the CTA drains its TMA copies,
 // frees its TMEM and returns, and tl_device_status() reports TL_ETIMEOUT.
@@ -47,7 +51,12 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 32;                 // k per stage
-constexpr int kThreads = 320;
+constexpr int kConvWarps = 8;
+constexpr int kEpiWarps = 8;
+constexpr int kConvThreads = 32 * kConvWarps;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kEpiWarp0 = 2 + kConvWarps;
+constexpr int kThreads = 32 * (2 + kConvWarps + kEpiWarps);
 constexpr int kTmemCols = 512;
 constexpr long long kTimeoutCycles = 4000000000LL;   // about 2 s at 2 GHz
 
@@ -242,6 +251,7 @@ struct TcArgs {
     int ns_stg, ns_op;
     int nacc;                // TMEM accumulator buffers (2 when Jp <= 256)
     int accumulate;
+    int vec_out;             // j contiguous in C, 16-byte aligned rows: float4 stores
     int64_t ntiles;
     int64_t M;               // ROW: rows; COL: inner extent
     int64_t tiles_per_o;     // COL
@@ -304,15 +314,15 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.ns_stg; ++s) {
             mbar_init(bars.stg_full + 8 * s, 1);
-            mbar_init(bars.stg_empty + 8 * s, 128);
+            mbar_init(bars.stg_empty + 8 * s, kConvThreads);
         }
         for (int s = 0; s < a.ns_op; ++s) {
-            mbar_init(bars.op_full + 8 * s, 1 + 128);
+            mbar_init(bars.op_full + 8 * s, 1 + kConvThreads);
             mbar_init(bars.op_empty + 8 * s, 1);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(bars.acc_full + 8 * s, 1);
-            mbar_init(bars.acc_empty + 8 * s, 128);
+            mbar_init(bars.acc_empty + 8 * s, kEpiThreads);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
@@ -432,9 +442,12 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
                 acc.next(a.nacc);
             }
         }
-    } else if (warp < 6) {
+    } else if (warp < kEpiWarp0) {
         // ------------------------------------------------------ converters
-        const int t = threadIdx.x - 64;          // operand row 0..127
+        const int tc = threadIdx.x - 64;
+        const int t = tc & (BM - 1);             // operand row 0..127
+        const int kh = tc >> 7;                  // which half of the 32 k values
+        constexpr int KH = BK / 2;
         Pipe st, op;
         bool ok = true;
         for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
@@ -443,17 +456,17 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
                 if (!(ok = mbar_wait(bars.op_empty + 8 * op.idx, op.phase ^ 1u))) break;
                 const float* stg = reinterpret_cast<const float*>(
                     sbase + a.off_stg + st.idx * a.a_stage_bytes);
-                float x[BK];
+                float x[KH];
                 if (a.variant == V_COL) {
-                    // staging is [BK k][128 i]: column t
+                    // staging is [BK k][128 i]: column t, k in this half
 #pragma unroll
-                    for (int k = 0; k < BK; ++k) x[k] = stg[k * BM + t];
+                    for (int k = 0; k < KH; ++k) x[k] = stg[(kh * KH + k) * BM + t];
                 } else {
                     // staging is [128 m][BK k] with 128-byte swizzle
                     const float4* row = reinterpret_cast<const float4*>(stg + t * BK);
 #pragma unroll
-                    for (int c = 0; c < BK / 4; ++c) {
-                        float4 v = row[c ^ (t & 7)];
+                    for (int c = 0; c < KH / 4; ++c) {
+                        float4 v = row[(kh * (KH / 4) + c) ^ (t & 7)];
                         x[4 * c] = v.x;
                         x[4 * c + 1] = v.y;
                         x[4 * c + 2] = v.z;
@@ -464,28 +477,29 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
                 uint8_t* pa0 = sbase + (op_a(op.idx, 0) - base) + row_off;
                 if constexpr (kTF32) {
 #pragma unroll
-                    for (int c = 0; c < kChunks; ++c) {
+                    for (int c = 0; c < KH / 4; ++c) {
                         uint4 v = make_uint4(to_tf32(x[4 * c]), to_tf32(x[4 * c + 1]),
                                              to_tf32(x[4 * c + 2]), to_tf32(x[4 * c + 3]));
-                        *reinterpret_cast<uint4*>(pa0 + c * 128) = v;
+                        *reinterpret_cast<uint4*>(pa0 + (kh * (KH / 4) + c) * 128) = v;
                     }
                 } else {
                     uint8_t* pa1 = sbase + (op_a(op.idx, kParts - 1) - base) + row_off;
 #pragma unroll
-                    for (int c = 0; c < kChunks; ++c) {
+                    for (int c = 0; c < KH / 8; ++c) {
                         float h[8], l[8];
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
                             h[e] = __bfloat162float(__float2bfloat16_rn(x[8 * c + e]));
                             l[e] = x[8 * c + e] - h[e];
                         }
+                        const int oc = kh * (KH / 8) + c;
                         uint4 vh = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]),
                                               pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
-                        *reinterpret_cast<uint4*>(pa0 + c * 128) = vh;
+                        *reinterpret_cast<uint4*>(pa0 + oc * 128) = vh;
                         if constexpr (kParts == 2) {
                             uint4 vl = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]),
                                                   pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
-                            *reinterpret_cast<uint4*>(pa1 + c * 128) = vl;
+                            *reinterpret_cast<uint4*>(pa1 + oc * 128) = vl;
                         }
                     }
                 }
@@ -499,9 +513,9 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
     } else {
         // ------------------------------------------------------ epilogue
         const int quarter = warp & 3;
-        const int row = quarter * 32 + lane;
+        const int chalf = (warp - kEpiWarp0) >> 2;   // this warp's 32-column chunks
         // per-warp 32 x 33 staging tile: rows are TMEM lanes, columns j
-        float* tile = reinterpret_cast<float*>(sbase + a.off_epi) + (warp - 6) * 32 * 33;
+        float* tile = reinterpret_cast<float*>(sbase + a.off_epi) + (warp - kEpiWarp0) * 32 * 33;
         // j contiguous in C (and not i): transpose so that lanes run along j
         const bool j_fast = (a.scq == 1);
         Pipe acc;
@@ -519,10 +533,35 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
             }
             nrows = a.M - rbase;               // rows of this warp that exist (may be <= 0)
             const uint32_t tcol = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc.idx * acc_cols;
-            for (int c0 = 0; c0 < a.Jp; c0 += 32) {
+            for (int c0 = 32 * chalf; c0 < a.Jp; c0 += 64) {
                 float v[32];
                 tmem_ld32(tcol + c0, v);
-                if (j_fast) {
+                if (j_fast && a.vec_out) {
+                    // 32 x 32 tile with 16-byte chunks XOR-swizzled by row: both the
+                    // row-wise writes and the chunk-wise reads are conflict-free
+                    float4* t4 = reinterpret_cast<float4*>(tile);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        t4[lane * 8 + (c ^ (lane & 7))] =
+                            make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                    __syncwarp();
+                    const int cc = lane & 7;
+                    const int jg = c0 + 4 * cc;
+#pragma unroll
+                    for (int it = 0; it < 8; ++it) {
+                        const int r = it * 4 + (lane >> 3);
+                        float4 x = t4[r * 8 + (cc ^ (r & 7))];
+                        if (r < nrows && jg < a.J) {
+                            float4* p = reinterpret_cast<float4*>(a.C + obase + (rbase + r) * a.sc_m + jg);
+                            if (a.accumulate) {
+                                float4 o = *p;
+                                x.x += o.x; x.y += o.y; x.z += o.z; x.w += o.w;
+                            }
+                            *p = x;
+                        }
+                    }
+                    __syncwarp();
+                } else if (j_fast) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = v[j];
                     __syncwarp();
@@ -643,7 +682,7 @@ Layout layout_for(const TtmPlan& P)
     L.opa_part = BM * BK * L.esize;
     L.opb_part = (uint32_t)L.Jp * BK * L.esize;
     L.op_stage = L.nparts * (L.opa_part + L.opb_part);
-    const uint32_t epi = 4 * 32 * 33 * 4;                // epilogue transpose tiles
+    const uint32_t epi = kEpiWarps * 32 * 33 * 4;        // epilogue transpose tiles
     const uint32_t budget = 227 * 1024 - 1024 - 512 - epi;   // alignment slack + barriers
     // FP32 staging keeps the HBM bytes in flight; the operand ring only has
     // to cover the convert -> MMA hand-off
@@ -688,6 +727,13 @@ int launch_prec(const TtmPlan& P, const void* A, const void* B, void* C, int acc
     a.accumulate = accumulate;
     a.scq = P.scq;
     a.a_stage_bytes = L.a_stage;
+    {
+        const int64_t scm = P.tc_variant == V_ROW ? (P.rows.nd ? P.rows.d[0].s[1] : 0)
+                                                  : P.rows.d[0].s[1];
+        a.vec_out = (P.scq == 1 && P.J % 4 == 0 && scm % 4 == 0 &&
+                     (P.tc_variant != V_COL || P.rows.nd < 2 || P.rows.d[1].s[1] % 4 == 0) &&
+                     (reinterpret_cast<uintptr_t>(C) % 16) == 0) ? 1 : 0;
+    }
     a.opa_part_bytes = L.opa_part;
     a.opb_part_bytes = L.opb_part;
     a.off_stg = L.off_stg;

@@ -16,10 +16,16 @@
 // kernel adds them in split order (deterministic).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "device.cuh"
 #include "kernels.h"
+#include "pipeline.cuh"
 
 namespace tl {
+
+// Set when a bounded wait of a pipelined ttv kernel gives up.
+__device__ unsigned int g_ttv_status;
 
 namespace {
 
@@ -35,30 +41,40 @@ struct TtvArgs {
 
 constexpr int kThreads = 256;
 
-// Sums 4 per-lane partials over groups of L lanes with a halving butterfly
-// (6 shuffles for L = 32 instead of 4 x 5): afterwards the lane with
-// sub-lane index s holds the total of row 2*(s >= L/2) + ((s & L/4) != 0).
-template <typename T, int L>
-__device__ __forceinline__ T reduce4(T a0, T a1, T a2, T a3, int sub)
+// Sums R (4 or 8) per-lane partials over groups of L lanes with a halving
+// butterfly: at each of the first log2(R) levels a lane keeps the half of the
+// rows its partner does not, so R = 8 over 32 lanes takes 9 shuffles instead
+// of 40.  Afterwards the lane with sub-lane index s holds the total of row
+// sum_l ((s & (L >> (l+1))) != 0) << (log2(R) - 1 - l).
+template <typename T, int L, int R>
+__device__ __forceinline__ T reduce_rows(T* v, int sub)
 {
-    constexpr int h = L / 2, h2 = L / 4;
-    const bool up = (sub & h) != 0;
-    T y0 = __shfl_xor_sync(0xffffffffu, up ? a0 : a2, h);
-    T y1 = __shfl_xor_sync(0xffffffffu, up ? a1 : a3, h);
-    T k0 = (up ? a2 : a0) + y0;
-    T k1 = (up ? a3 : a1) + y1;
-    const bool up2 = (sub & h2) != 0;
-    T y = __shfl_xor_sync(0xffffffffu, up2 ? k0 : k1, h2);
-    T r = (up2 ? k1 : k0) + y;
+    int cnt = R;
 #pragma unroll
-    for (int m = h2 / 2; m >= 1; m /= 2) r += __shfl_xor_sync(0xffffffffu, r, m);
+    for (int lvl = 0; (R >> lvl) > 1; ++lvl) {
+        const int h = L >> (lvl + 1);
+        const bool up = (sub & h) != 0;
+        const int half = cnt / 2;
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {
+            if (i < half) {
+                T send = up ? v[i] : v[i + half];
+                T keep = up ? v[i + half] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+            }
+        }
+        cnt = half;
+    }
+    T r = v[0];
+    constexpr int kLevels = (R == 8) ? 3 : 2;
+#pragma unroll
+    for (int m = (L >> kLevels) / 2; m >= 1; m /= 2) r += __shfl_xor_sync(0xffffffffu, r, m);
     return r;
 }
 
-template <typename T, int VEC, int L>
+template <typename T, int VEC, int L, int R>
 __global__ void __launch_bounds__(kThreads) ttv_row_kernel(const TtvArgs a)
 {
-    constexpr int R = 4;
     const T* __restrict__ A = static_cast<const T*>(a.A);
     const T* __restrict__ b = static_cast<const T*>(a.b);
     const int lane = threadIdx.x & 31;
@@ -104,9 +120,10 @@ __global__ void __launch_bounds__(kThreads) ttv_row_kernel(const TtvArgs a)
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) acc[r] = fma(va[r][v], vb[v], acc[r]);
             }
-            const T tot = reduce4<T, L>(acc[0], acc[1], acc[2], acc[3], sub);
-            if ((sub & (L / 4 - 1)) == 0) {
-                const int rs = 2 * ((sub & (L / 2)) != 0) + ((sub & (L / 4)) != 0);
+            const T tot = reduce_rows<T, L, R>(acc, sub);
+            constexpr int kG = L / R;                 // lanes per row after the butterfly
+            if ((sub & (kG - 1)) == 0) {
+                const int rs = sub / kG;
                 int64_t rw = 0;
                 bool okw = false;
 #pragma unroll
@@ -124,6 +141,111 @@ __global__ void __launch_bounds__(kThreads) ttv_row_kernel(const TtvArgs a)
                 }
             }
         }
+    }
+}
+
+// Row case with dense rows (w_q = 1 and consecutive outputs n_q apart): the
+// rows are one contiguous stream, so a producer thread moves blocks of rows
+// with 1-D bulk copies into a 3-stage shared-memory ring (16 KB stages) and
+// eight consumer warps reduce them from shared memory (b is staged once per
+// CTA).  Three CTAs per SM: measured on GB300, the consumers of a single CTA
+// per SM cannot keep up (3.1 TB/s) while three CTAs stream at 6.7 TB/s.
+struct RowStageArgs {
+    const void* A;
+    const void* b;
+    void* C;
+    int64_t rows, nq, sc;
+    int rows_per_stage, nstages;
+    uint32_t stage_bytes, off_b, off_bar;
+    int accumulate;
+};
+
+constexpr int kStageConsumers = 8;                      // consumer warps
+constexpr int kStageThreads = 32 * (kStageConsumers + 1);
+
+template <typename T>
+__global__ void __launch_bounds__(kStageThreads, 3) ttv_row_staged_kernel(const RowStageArgs a)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    constexpr int VEC = 16 / sizeof(T);
+    using VT = typename Vec<T, VEC>::type;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t base = pipe::smem_u32(smem);
+    const uint32_t full = base + a.off_bar, empty = full + 8 * a.nstages;
+    const T* sb = reinterpret_cast<const T*>(smem + a.off_b);
+    const int64_t nchunks = (a.rows + a.rows_per_stage - 1) / a.rows_per_stage;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.nstages; ++s) {
+            pipe::mbar_init(full + 8 * s, 1);
+            pipe::mbar_init(empty + 8 * s, kStageConsumers);
+        }
+        pipe::mbar_init_fence();
+        pipe::fence_proxy_async();
+    }
+    for (int64_t k = threadIdx.x; k < a.nq; k += kStageThreads)
+        const_cast<T*>(sb)[k] = static_cast<const T*>(a.b)[k];
+    __syncthreads();
+
+    if (warp == kStageConsumers) {
+        if (lane == 0) {
+            pipe::Ring r;
+            bool ok = true;
+            uint32_t armed = 0, par = 0;
+            const size_t row_bytes = (size_t)a.nq * sizeof(T);
+            for (int64_t c = blockIdx.x; c < nchunks && ok; c += gridDim.x) {
+                if (!(ok = pipe::mbar_wait(empty + 8 * r.idx, r.phase ^ 1u, &g_ttv_status))) break;
+                const int64_t r0 = c * a.rows_per_stage;
+                const int64_t nr = min((int64_t)a.rows_per_stage, a.rows - r0);
+                const uint32_t bytes = (uint32_t)(nr * row_bytes);
+                pipe::mbar_arrive_tx(full + 8 * r.idx, bytes);
+                pipe::bulk_load(base + r.idx * a.stage_bytes,
+                                static_cast<const T*>(a.A) + r0 * a.nq, bytes, full + 8 * r.idx);
+                armed |= 1u << r.idx;
+                par = (par & ~(1u << r.idx)) | (r.phase << r.idx);
+                r.next(a.nstages);
+            }
+            if (!ok)
+                for (int s = 0; s < a.nstages; ++s)
+                    if (armed & (1u << s)) pipe::mbar_drain(full + 8 * s, (par >> s) & 1u);
+        }
+        return;
+    }
+    // consumers: warp w takes rows w, w + 8, ... of each staged block, four at a time
+    pipe::Ring r;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        if (!pipe::mbar_wait(full + 8 * r.idx, r.phase, &g_ttv_status)) break;
+        const int64_t r0 = c * a.rows_per_stage;
+        const int nr = (int)min((int64_t)a.rows_per_stage, a.rows - r0);
+        const T* st = reinterpret_cast<const T*>(smem + r.idx * a.stage_bytes);
+        for (int g0 = warp * 4; g0 < nr; g0 += kStageConsumers * 4) {
+            T acc[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                acc[i] = T(0);
+                const int row = g0 + i;
+                if (row < nr) {
+                    for (int64_t kk = (int64_t)lane * VEC; kk < a.nq; kk += 32 * VEC) {
+                        VT x = *reinterpret_cast<const VT*>(st + (int64_t)row * a.nq + kk);
+                        VT y = *reinterpret_cast<const VT*>(sb + kk);
+                        const T* xe = reinterpret_cast<const T*>(&x);
+                        const T* ye = reinterpret_cast<const T*>(&y);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[i] = fma(xe[v], ye[v], acc[i]);
+                    }
+                }
+            }
+            const T tot = reduce_rows<T, 32, 4>(acc, lane);
+            if ((lane & 7) == 0) {
+                const int row = g0 + (lane >> 3);
+                if (row < nr) {
+                    T* pc = static_cast<T*>(a.C) + (r0 + row) * a.sc;
+                    *pc = a.accumulate ? *pc + tot : tot;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) pipe::mbar_arrive(empty + 8 * r.idx);
+        r.next(a.nstages);
     }
 }
 
@@ -226,10 +348,40 @@ int launch_typed(const TtvPlan& P, const void* A, const void* b, void* C, void* 
     a.splits = P.splits;
     a.accumulate = accumulate;
     constexpr int V = 16 / sizeof(T);
+    if (P.kernel == K_TTV_ROW && P.splits == 1 && P.vec == V && P.nq % (32 * V) == 0 &&
+        P.out.nd == 1 && P.out.d[0].s[0] == P.nq && P.nq * (int64_t)sizeof(T) <= 8192 &&
+        P.incb == 1 && aligned(b, 16)) {
+        RowStageArgs r{};
+        r.A = A;
+        r.b = b;
+        r.C = C;
+        r.rows = P.nout;
+        r.nq = P.nq;
+        r.sc = P.out.d[0].s[1];
+        r.accumulate = accumulate;
+        const int64_t row_bytes = P.nq * (int64_t)sizeof(T);
+        // about 16 KB per stage, a multiple of 4 rows (row_bytes <= 8 KB)
+        r.rows_per_stage = (int)std::max<int64_t>(4, std::min<int64_t>(256, (16 * 1024) / row_bytes) / 4 * 4);
+        r.nstages = 3;
+        r.stage_bytes = (uint32_t)(r.rows_per_stage * row_bytes);
+        r.off_b = r.nstages * r.stage_bytes;
+        r.off_bar = r.off_b + (uint32_t)((row_bytes + 127) / 128 * 128);
+        const uint32_t smem = r.off_bar + 16 * r.nstages;
+        static bool attr_set[2] = {false, false};
+        if (!attr_set[sizeof(T) == 8]) {
+            cudaFuncSetAttribute(ttv_row_staged_kernel<T>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            attr_set[sizeof(T) == 8] = true;
+        }
+        const int64_t nchunks = (P.nout + r.rows_per_stage - 1) / r.rows_per_stage;
+        const int grid = (int)std::min<int64_t>(nchunks, (int64_t)num_sms * 3);
+        ttv_row_staged_kernel<T><<<grid, kStageThreads, smem, st>>>(r);
+        return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
+    }
     if (P.kernel == K_TTV_ROW) {
         int64_t threads = (P.nout + 3) / 4 * P.lanes;
         int grid = grid_for(threads, num_sms);
-#define TL_ROW(VV, LL) ttv_row_kernel<T, VV, LL><<<grid, kThreads, 0, st>>>(a)
+#define TL_ROW(VV, LL) ttv_row_kernel<T, VV, LL, 4><<<grid, kThreads, 0, st>>>(a)
         if (P.vec == V) {
             switch (P.lanes) {
             case 32: TL_ROW(V, 32); break;
@@ -259,6 +411,20 @@ int launch_typed(const TtvPlan& P, const void* A, const void* b, void* C, void* 
 }
 
 }  // namespace
+
+int ttv_status(bool clear)
+{
+    unsigned int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_ttv_status, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return TL_ECUDA;
+    }
+    if (clear && v) {
+        unsigned int z = 0;
+        cudaMemcpyToSymbol(g_ttv_status, &z, sizeof z);
+    }
+    return v ? TL_ETIMEOUT : TL_OK;
+}
 
 size_t ttv_workspace_bytes(const TtvPlan& P)
 {

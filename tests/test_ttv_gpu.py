@@ -54,7 +54,8 @@ def test_ttv_integer_inputs_bit_exact(tl, cuda_dev, dtype):
 
 
 @pytest.mark.parametrize("shape", [(129, 67, 33), (1000, 257), (5, 3, 7001), (70, 1, 90, 3),
-                                   (33, 17, 9, 5, 3), (4097, 3, 2)])
+                                   (33, 17, 9, 5, 3), (4097, 3, 2), (128, 1001), (2048, 77),
+                                   (256, 3, 700)])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_ttv_multi_tile_ragged_all_modes(tl, cuda_dev, shape, dtype):
     X = synth.normal(shape, 1500, dtype=np.float64)
@@ -171,3 +172,13 @@ def test_ttv_full_scale_sampled(tl, cuda_dev, scale_tensors):
             ref = oracle.ttv_at(mem, n, wA, q, case.vectors[q - 1], idx)
             sample = got[tuple(idx.T)]
             assert rel_err(sample, ref) <= 1e-5, (pi, q)
+
+
+def test_ttv_staged_row_kernel_selected_and_exact_on_integers(tl, cuda_dev):
+    # dense rows (q fastest), n_q a multiple of 128: the bulk-copy staged path
+    for dtype, n in (("f32", (128, 3001)), ("f64", (256, 999)), ("f32", (2048, 50))):
+        X = synth.integers(n, 1950)
+        b = synth.integers((n[0],), 1951)
+        got, ref = ttv_case(tl, cuda_dev, X, 1, b, (1, 2), (1,), dtype)
+        np.testing.assert_array_equal(got, ref)
+    assert tl.tl_device_status() == tl.TL_OK
