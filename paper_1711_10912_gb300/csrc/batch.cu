@@ -242,8 +242,12 @@ __device__ void run_unit(const BOp& op, int64_t u, uint8_t* smem)
     case BV_TTV_ROW4: unit_ttv_row<T, 4>(op, e0, e1); break;
     case BV_TTV_ROW8: unit_ttv_row<T, 8>(op, e0, e1); break;
     case BV_TTV_ROW32: unit_ttv_row<T, 32>(op, e0, e1); break;
-    case BV_TTM_32: unit_ttm<T, 32>(op, e0, smem); break;
-    case BV_TTM_64: unit_ttm<T, 64>(op, e0, smem); break;
+    case BV_TTM_32:
+        for (int64_t m0 = e0; m0 < e1; m0 += 32) unit_ttm<T, 32>(op, m0, smem);
+        break;
+    case BV_TTM_64:
+        for (int64_t m0 = e0; m0 < e1; m0 += 64) unit_ttm<T, 64>(op, m0, smem);
+        break;
     default: unit_ew<T>(op, e0, e1); break;
     }
 }
@@ -258,29 +262,38 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BOp* __restrict__
     __shared__ __align__(16) BOp sop;
     __shared__ int64_t s_unit;
     __shared__ int s_op;
+    int cur = -1;                        // operation held in sop (same in every thread)
+    int hint = 0;                        // thread 0: search start
     for (;;) {
         if (threadIdx.x == 0) {
             int64_t u = (int64_t)atomicAdd(counter, 1ull);
             s_unit = u;
             if (u < total_units) {
-                int lo = 0, hi = nops - 1;          // last op with ubegin <= u
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) / 2;
-                    if (ops[mid].ubegin <= u) lo = mid;
-                    else hi = mid - 1;
+                // the counter only grows, so the owner of u is at or after the
+                // owner of this CTA's previous unit: scan forward, then bisect
+                int lo = hint;
+                if (lo + 1 < nops && ops[lo + 1].ubegin <= u) {
+                    int hi = nops - 1;
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) / 2;
+                        if (ops[mid].ubegin <= u) lo = mid;
+                        else hi = mid - 1;
+                    }
                 }
                 s_op = lo;
+                hint = lo;
             }
         }
         __syncthreads();
         const int64_t u = s_unit;
         if (u >= total_units) break;
-        {
-            const uint32_t* src = reinterpret_cast<const uint32_t*>(ops + s_op);
+        if (s_op != cur) {
+            cur = s_op;
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(ops + cur);
             uint32_t* dst = reinterpret_cast<uint32_t*>(&sop);
             for (int i = threadIdx.x; i < (int)(sizeof(BOp) / 4); i += kThreads) dst[i] = src[i];
+            __syncthreads();
         }
-        __syncthreads();
         if (sop.dtype == TL_F64) run_unit<double>(sop, u, smem);
         else run_unit<float>(sop, u, smem);
         __syncthreads();
@@ -309,14 +322,16 @@ std::vector<Candidate> candidates(const BOp& op)
     if (op.kind == TL_OP_TTV) {
         if (op.saq == 1) {
             for (int32_t v : {BV_TTV_ROW4, BV_TTV_ROW8, BV_TTV_ROW32})
-                for (int64_t u : {256, 1024}) c.push_back({v, u});
+                for (int64_t u : {512, 4096}) c.push_back({v, u});
         }
-        for (int64_t u : {256, 1024, 4096}) c.push_back({BV_TTV_COL, u});
+        for (int64_t u : {1024, 4096, 16384}) c.push_back({BV_TTV_COL, u});
     } else if (op.kind == TL_OP_TTM) {
-        c.push_back({BV_TTM_32, 32});
-        c.push_back({BV_TTM_64, 64});
+        for (int64_t u : {256, 1024, 4096}) {
+            c.push_back({BV_TTM_32, u});
+            c.push_back({BV_TTM_64, u});
+        }
     } else {
-        for (int64_t u : {1024, 8192}) c.push_back({BV_EW, u});
+        for (int64_t u : {8192, 65536}) c.push_back({BV_EW, u});
     }
     return c;
 }
@@ -325,11 +340,11 @@ std::vector<Candidate> candidates(const BOp& op)
 Candidate heuristic(const BOp& op)
 {
     if (op.kind == TL_OP_TTV) {
-        if (op.saq == 1 && op.nq >= 32) return {BV_TTV_ROW8, 256};
-        return {BV_TTV_COL, 1024};
+        if (op.saq == 1 && op.nq >= 32) return {BV_TTV_ROW8, 2048};
+        return {BV_TTV_COL, 4096};
     }
-    if (op.kind == TL_OP_TTM) return op.count >= 4096 ? Candidate{BV_TTM_64, 64} : Candidate{BV_TTM_32, 32};
-    return {BV_EW, 8192};
+    if (op.kind == TL_OP_TTM) return op.count >= 4096 ? Candidate{BV_TTM_64, 1024} : Candidate{BV_TTM_32, 256};
+    return {BV_EW, 65536};
 }
 
 struct TuneCache {
@@ -704,7 +719,10 @@ int batch_set_variant(Batch* B, int32_t kind, int32_t variant, int64_t unit, voi
         (kind == TL_OP_TTM && (variant == BV_TTM_32 || variant == BV_TTM_64)) ||
         (kind == TL_OP_ENTRYWISE && variant == BV_EW);
     if (!ok_kind) return TL_EINVAL;
-    if (kind == TL_OP_TTM) unit = variant == BV_TTM_32 ? 32 : 64;   // a ttm unit is one row tile
+    if (kind == TL_OP_TTM) {          // a ttm unit is a whole number of row tiles
+        const int64_t bm = variant == BV_TTM_32 ? 32 : 64;
+        unit = (unit + bm - 1) / bm * bm;
+    }
     for (BOp& b : B->host)
         if (b.kind == kind) {
             b.variant = variant;
