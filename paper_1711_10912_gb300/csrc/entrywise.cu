@@ -12,6 +12,8 @@
 //               that input), transposed in shared memory and written along
 //               dim 0 (coalesced for C); an input already contiguous along
 //               dim 0 is read directly in the write phase.
+//   ew_rows     every operand is contiguous along dim 0 but the other dims
+//               are ordered differently: one offset decode per 16-byte vector.
 //   ew_generic  anything else: each element's offsets come from the mapper.
 #include <cuda_runtime.h>
 
@@ -106,6 +108,31 @@ __global__ void __launch_bounds__(kThreads) ew_generic_kernel(const EwArgs a)
         T x = __ldg(A + off[0]);
         T y = unary ? T(0) : __ldg(B + off[1]);
         C[off[2]] = apply<T>(a.op, x, y, alpha);
+    }
+}
+
+// All operands unit-stride along dim 0 but laid out differently in the other
+// dims: one offset decode per 16-byte vector along dim 0, vector loads and
+// stores (dim 0's extent and every other stride are multiples of VEC).
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kThreads) ew_rows_kernel(const EwArgs a)
+{
+    const T* __restrict__ A = static_cast<const T*>(a.A);
+    const T* __restrict__ B = static_cast<const T*>(a.B);
+    T* __restrict__ C = static_cast<T*>(a.C);
+    const T alpha = (T)a.alpha;
+    const bool unary = (a.op == TL_COPY || a.op == TL_SCALE);
+    const int64_t nvec = a.N / VEC;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < nvec; g += stride) {
+        int64_t off[3];
+        map_offsets<3>(a.sp, g, VEC, off);
+        T x[VEC], y[VEC], r[VEC];
+        vload_stream<T, VEC>(A + off[0], x);
+        if (!unary) vload_stream<T, VEC>(B + off[1], y);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) r[v] = apply<T>(a.op, x[v], unary ? T(0) : y[v], alpha);
+        vstore<T, VEC>(C + off[2], r);
     }
 }
 
@@ -307,6 +334,8 @@ int launch_typed(const EwPlan& P, const void* A, const void* B, double alpha, vo
         int grid = (int)(total < cap ? total : cap);
         if (P.vec > 1) ew_tile_vec_kernel<T><<<grid, kThreads, 0, st>>>(a, tiles0, tiles1, batch);
         else ew_tile_kernel<T><<<grid, kThreads, 0, st>>>(a, tiles0, tiles1, batch);
+    } else if (P.kernel == K_EW_ROWS) {
+        ew_rows_kernel<T, V><<<grid_for(P.N / V, num_sms), kThreads, 0, st>>>(a);
     } else {
         ew_generic_kernel<T><<<grid_for(P.N, num_sms), kThreads, 0, st>>>(a);
     }

@@ -125,6 +125,7 @@ const char* kernel_name(int k)
     case K_EW_FLAT: return "ew_flat";
     case K_EW_TILE: return "ew_tile";
     case K_EW_GENERIC: return "ew_generic";
+    case K_EW_ROWS: return "ew_rows";
     case K_TTM_SIMT: return "ttm_simt";
     case K_TTM_TC: return "ttm_tc";
     default: return "none";
@@ -317,6 +318,19 @@ int plan_entrywise(int32_t op, const Tensor& A, const Tensor* B, const Tensor& C
         P.vec = v ? V : 1;
     } else {
         P.kernel = K_EW_GENERIC;
+        // every operand contiguous along dim 0: decode once per 16-byte vector
+        const Space& sp = P.sp;
+        bool v = sp.nd >= 1 && sp.d[0].n % V == 0 && aligned(A.data, 16) && aligned(C.data, 16) &&
+                 (!B || aligned(B->data, 16));
+        for (int o = 0; o < 3 && v; ++o) {
+            if (o == 1 && !B) continue;
+            v = sp.d[0].s[o] == 1;
+            for (int d = 1; d < sp.nd && v; ++d) v = sp.d[d].s[o] % V == 0;
+        }
+        if (v) {
+            P.kernel = K_EW_ROWS;
+            P.vec = V;
+        }
     }
     return TL_OK;
 }

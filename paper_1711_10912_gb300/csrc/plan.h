@@ -76,6 +76,7 @@ enum Kernel : int {
     K_EW_FLAT,        // all operands share one contiguous layout
     K_EW_TILE,        // two fastest dims differ: smem-tiled transpose
     K_EW_GENERIC,     // any strides: per-element offset mapping
+    K_EW_ROWS,        // all contiguous along dim 0, other dims permuted: per-vector mapping
     K_TTM_SIMT,       // register-tiled FP32 / FP64 batched GEMM
     K_TTM_TC,         // tcgen05 tensor-core batched GEMM
 };

@@ -123,3 +123,21 @@ def test_entrywise_vector_tile_path_is_taken(tl, cuda_dev):
                                      tl.Desc(B, n, (3, 2, 1)), 0, 0, 0, 0, tl.Desc(C, n))
         P = json.loads(js)
         assert P["kernel"] == "ew_tile" and P["vec"] == (4 if dtype == "f32" else 2), P
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_entrywise_shared_fastest_mode_rows_path(tl, cuda_dev, dtype):
+    # same fastest mode, the other modes permuted: the per-vector mapper path
+    import json
+    n = (12, 5, 7, 3)
+    X = synth.normal(n, 3500, dtype=np.float64)
+    Y = synth.normal(n, 3501, dtype=np.float64)
+    for pa, pb, pc in [((1, 3, 2, 4), (1, 2, 3, 4), (1, 4, 3, 2)), ((1, 2, 3, 4), (1, 4, 2, 3), (1, 2, 4, 3))]:
+        A = put(X, pa, cuda_dev, dtype)
+        B = put(Y, pb, cuda_dev, dtype)
+        C = torch.empty_like(A)
+        rc, js = tl.tl_plan_describe(tl.TL_OP_ENTRYWISE, tl.Desc(A, n, pa), tl.Desc(B, n, pb),
+                                     0, 0, 0, tl.TL_MUL, tl.Desc(C, n, pc))
+        assert json.loads(js)["kernel"] == "ew_rows", js
+        got, ref = ew_case(tl, cuda_dev, OPS["mul"], X, Y, pa, pb, pc, dtype)
+        np.testing.assert_array_equal(got, ref)
