@@ -24,6 +24,11 @@ Parity status of each function (how it is pinned, see tests/test_oracle_*.py):
                          the p=2 matrix product, mode commutation, tensordot.
   entrywise              pinned by numpy elementwise ops on logical arrays.
   norm, rel_error        pinned by numpy.linalg.norm and closed forms.
+  ttvs, ttms             compositions of ttv / ttm; pinned by numpy einsum, a
+                         rank-1 closed form and order independence.
+  hopm                   pinned by one-sweep convergence on rank-1 tensors
+                         (lambda = sigma) and by p = 2 power iteration against
+                         numpy's largest singular value.
 """
 from __future__ import annotations
 
@@ -290,3 +295,65 @@ def rel_error(X, wX, R, wR, n) -> float:
     return float(_load().orc_rel_error(len(n_), _ptr(n_, ctypes.c_int64),
                                        _ptr(Xb, ctypes.c_double), _ptr(wX_, ctypes.c_int64),
                                        _ptr(Rb, ctypes.c_double), _ptr(wR_, ctypes.c_int64)))
+
+
+# ------------------------------------------------- sequences and HOPM ---
+
+def ttvs(A, n, wA, modes, vecs, offA=0):
+    """Tensor times several vectors (Sec. 5.2 Table 3, times_vectors): A is
+    contracted with vecs[j] along the distinct 1-based modes[j], applying the
+    vectors from the last listed to the first (the order the paper states for
+    times_vectors, so the remaining mode numbers stay valid).  Each step is
+    one oracle ttv (Eq. 24) into a dense first-order FP64 intermediate.
+    Returns (buffer, extents of the remaining modes in order)."""
+    n = [int(x) for x in n]
+    modes = [int(m) for m in modes]
+    if len(set(modes)) != len(modes) or any(m < 1 or m > len(n) for m in modes):
+        raise ValueError("modes must be distinct and within 1..p")
+    if len(modes) >= len(n):
+        raise ValueError("a sequence of ttv (Eq. 24, order >= 2) leaves at least one mode")
+    cur, cur_n, cur_w, cur_off = A, list(n), list(wA), offA
+    alive = list(range(1, len(n) + 1))          # original mode numbers still present
+    for m, v in reversed(list(zip(modes, vecs))):
+        q = alive.index(m) + 1
+        out = ttv(cur, cur_n, cur_w, q, v, offA=cur_off)
+        del cur_n[q - 1]
+        alive.remove(m)
+        cur, cur_w, cur_off = out, list(strides(cur_n)) if cur_n else [], 0
+    return cur, tuple(cur_n)
+
+
+def ttms(A, n, wA, modes, mats, offA=0):
+    """Tensor times several matrices (Sec. 5.2 Table 3, times_matrices):
+    mats[j] is J_j x n_{modes[j]} (row-major); applied from the last listed to
+    the first, each step one oracle ttm (Eq. 25) into a dense first-order
+    FP64 intermediate.  Returns (buffer, output extents)."""
+    cur, cur_n, cur_w, cur_off = A, [int(x) for x in n], list(wA), offA
+    for m, M in reversed(list(zip(modes, mats))):
+        M = np.asarray(M)
+        J, K = M.shape
+        if K != cur_n[m - 1]:
+            raise ValueError("matrix columns must equal the mode's extent")
+        out = ttm(cur, cur_n, cur_w, m, M.reshape(-1), J, K, 1, offA=cur_off)
+        cur_n[m - 1] = J
+        cur, cur_w, cur_off = out, list(strides(cur_n)), 0
+    return cur, tuple(cur_n)
+
+
+def hopm(A, n, wA, u0, K):
+    """Higher-order power method for the best rank-1 approximation, following
+    the paper's listing in Sec. 5.2 (after De Lathauwer et al.): K sweeps; in
+    each, for r = 1..p, u_r <- A times all vectors except u_r (times_vectors
+    with mode r excluded), lambda_r <- ||u_r||, u_r <- u_r / lambda_r.
+    Returns (list of u vectors, list of lambdas), all FP64."""
+    p = len(n)
+    u = [np.asarray(x, dtype=np.float64).copy() for x in u0]
+    lam = [0.0] * p
+    for _ in range(int(K)):
+        for r in range(1, p + 1):
+            others = [m for m in range(1, p + 1) if m != r]
+            vec, rest = ttvs(A, n, wA, others, [u[m - 1] for m in others])
+            assert rest == (int(n[r - 1]),)
+            lam[r - 1] = norm(vec, rest, (1,))
+            u[r - 1] = vec / lam[r - 1]
+    return u, lam
