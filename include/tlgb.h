@@ -162,6 +162,42 @@ int tl_entrywise(int32_t op, const tl_tensor* A, const tl_tensor* B, double alph
                  const tl_tensor* C, void* stream);
 
 /*
+ * tl_ttvs -- tensor times several vectors (Sec. 5.2 Table 3, times_vectors):
+ * vecs[j] (device, n_{modes[j]} contiguous elements of A's dtype) along the
+ * distinct 1-based modes[j], applied from the last listed to the first (the
+ * order the paper states, which keeps the remaining mode numbers valid); at
+ * least one mode remains (count < p).  C: order p - count with A's remaining
+ * extents in order, any layout.  Each step is a tl_ttv; intermediates are
+ * dense, in the layout A's layout induces, in a per-stream workspace slot of
+ * the library (allocated on first need, like the split-K workspace).
+ * Errors: TL_EINVAL (repeated or out-of-range mode, count >= p, C's shape),
+ * TL_ENOMEM, TL_ECUDA.
+ */
+int tl_ttvs(const tl_tensor* A, const void* const* vecs, const uint32_t* modes, uint32_t count,
+            const tl_tensor* C, void* stream);
+
+/*
+ * tl_ttms -- tensor times several matrices (Sec. 5.2 Table 3,
+ * times_matrices; e.g. a Tucker projection): mats[j] (device, J[j] x
+ * n_{modes[j]}, row-major) along the distinct modes[j], last listed first.
+ * C: A's extents with n_{modes[j]} replaced by J[j].  precision as tl_ttm,
+ * for every step.  Intermediates as in tl_ttvs (A's layout).
+ */
+int tl_ttms(const tl_tensor* A, const void* const* mats, const int64_t* J, const uint32_t* modes,
+            uint32_t count, const tl_tensor* C, int32_t precision, void* stream);
+
+/*
+ * tl_hopm -- the higher-order power method of the paper's last listing
+ * (Sec. 5.2, best rank-1 approximation after De Lathauwer et al.): K sweeps;
+ * in each, for r = 1..p: u_r <- A times every u except u_r (tl_ttvs with
+ * mode r excluded), lambda_r <- ||u_r||_F (tl_norm, FP64), u_r <- u_r /
+ * lambda_r.  u[r] (device, n_r contiguous elements of A's dtype) hold the
+ * starting vectors and receive the results; lambda (device, p doubles)
+ * receives the last sweep's norms.  Everything stays on the device.
+ */
+int tl_hopm(const tl_tensor* A, void* const* u, double* lambda, uint32_t K, void* stream);
+
+/*
  * tl_norm -- Frobenius norm ||A||_F = sqrt(sum_i A(i)^2) (Table 3, norm),
  * accumulated in FP64 with a deterministic two-pass block reduction.
  * result: device pointer to three doubles, written asynchronously:

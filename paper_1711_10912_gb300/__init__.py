@@ -182,6 +182,13 @@ def _declare(_lib):
     _lib.tl_batch_set_variant.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int64, ctypes.c_void_p]
     _lib.tl_selftest_wait_timeout.argtypes = [ctypes.c_double, ctypes.c_void_p]
+    _lib.tl_ttvs.argtypes = [_T, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_uint32),
+                             ctypes.c_uint32, _T, ctypes.c_void_p]
+    _lib.tl_ttms.argtypes = [_T, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64),
+                             ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32, _T, ctypes.c_int32,
+                             ctypes.c_void_p]
+    _lib.tl_hopm.argtypes = [_T, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_uint32,
+                             ctypes.c_void_p]
 
 
 load_library()
@@ -226,6 +233,26 @@ def tl_ttm(A: Desc, B, J: int, ldb_row: int, ldb_col: int, q: int, C: Desc,
 
 def tl_entrywise(op: int, A: Desc, B, alpha: float, C: Desc, stream=None) -> int:
     return _lib.tl_entrywise(int(op), A.ref, _ref(B), float(alpha), C.ref, _stream(stream))
+
+
+def _ptr_array(xs):
+    return (ctypes.c_void_p * max(len(xs), 1))(*[_addr(x) for x in xs])
+
+
+def tl_ttvs(A: Desc, vecs, modes, C: Desc, stream=None) -> int:
+    m = (ctypes.c_uint32 * max(len(modes), 1))(*[int(x) for x in modes])
+    return _lib.tl_ttvs(A.ref, _ptr_array(vecs), m, len(modes), C.ref, _stream(stream))
+
+
+def tl_ttms(A: Desc, mats, J, modes, C: Desc, precision: int = TL_P_DEFAULT, stream=None) -> int:
+    m = (ctypes.c_uint32 * max(len(modes), 1))(*[int(x) for x in modes])
+    j = (ctypes.c_int64 * max(len(J), 1))(*[int(x) for x in J])
+    return _lib.tl_ttms(A.ref, _ptr_array(mats), j, m, len(modes), C.ref, int(precision),
+                        _stream(stream))
+
+
+def tl_hopm(A: Desc, u, lam, K: int, stream=None) -> int:
+    return _lib.tl_hopm(A.ref, _ptr_array(u), _addr(lam), int(K), _stream(stream))
 
 
 def tl_norm(A: Desc, result, stream=None) -> int:

@@ -46,7 +46,13 @@ namespace {
 struct WsKey {
     int dev;
     uintptr_t stream;
-    bool operator<(const WsKey& o) const { return dev != o.dev ? dev < o.dev : stream < o.stream; }
+    int slot;
+    bool operator<(const WsKey& o) const
+    {
+        if (dev != o.dev) return dev < o.dev;
+        if (stream != o.stream) return stream < o.stream;
+        return slot < o.slot;
+    }
 };
 struct WsBuf {
     void* ptr = nullptr;
@@ -56,13 +62,15 @@ std::mutex g_ws_mu;
 std::map<WsKey, WsBuf> g_ws;
 }  // namespace
 
-void* workspace(cudaStream_t st, size_t bytes)
+void* workspace(cudaStream_t st, size_t bytes) { return workspace_slot(st, bytes, 0); }
+
+void* workspace_slot(cudaStream_t st, size_t bytes, int slot)
 {
     if (bytes == 0) return nullptr;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
     std::lock_guard<std::mutex> lk(g_ws_mu);
-    WsBuf& b = g_ws[WsKey{dev, reinterpret_cast<uintptr_t>(st)}];
+    WsBuf& b = g_ws[WsKey{dev, reinterpret_cast<uintptr_t>(st), slot}];
     if (b.bytes >= bytes) return b.ptr;
     if (b.ptr) {
         // the old buffer may still be read by work queued on this stream

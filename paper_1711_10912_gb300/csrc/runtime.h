@@ -13,6 +13,10 @@ int device_sms();
 // Adds n to the process-wide launch counter reported by tl_launch_count().
 void count_launches(int n);
 void* workspace(cudaStream_t st, size_t bytes);
+// Independent per-(device, stream) buffers: slot 0 holds kernel partial sums
+// and converted operands; slot 1 the intermediates of operation sequences;
+// slot 2 small results of sequences (norms).
+void* workspace_slot(cudaStream_t st, size_t bytes, int slot);
 
 int prepare_ttv(const tl_tensor* A, const void* b, int64_t incb, uint32_t q, const tl_tensor* C,
                 int num_sms, Tensor& At, Tensor& Ct, TtvPlan& P);

@@ -231,3 +231,11 @@ def serving_stream(count: int, rate: float, seed: int = BASE_SEED + 5,
         pic = random_layout(p, g) if op == "entrywise" else ()
         out.append(Request(t, op, n, pi, q, dt, J, pib, pic, seed=int(g.integers(1 << 31))))
     return out
+
+
+def device_normal(torch, count: int, seed: int, dtype, device):
+    """N(0,1) values generated on the device from a seeded torch generator
+    (for operands too large to draw on the host quickly)."""
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return torch.randn(int(count), generator=g, dtype=dtype, device=device)
