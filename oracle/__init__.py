@@ -106,6 +106,12 @@ def _bind(path: str):
     lib.orc_entrywise.argtypes = [ctypes.c_int, ctypes.c_uint32, _i64p, _f64p, _i64p,
                                   _f64p, _i64p, ctypes.c_double, _f64p, _i64p]
     lib.orc_entrywise.restype = ctypes.c_int
+    lib.orc_transpose.argtypes = [ctypes.c_uint32, _i64p, _f64p, _i64p, _u32p, _f64p, _i64p]
+    lib.orc_transpose.restype = ctypes.c_int
+    lib.orc_ttt.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                            _i64p, _f64p, _i64p, _u32p, _i64p, _f64p, _i64p, _u32p,
+                            _f64p, _i64p, ctypes.c_int, ctypes.c_int]
+    lib.orc_ttt.restype = ctypes.c_int
     lib.orc_norm.argtypes = [ctypes.c_uint32, _i64p, _f64p, _i64p, ctypes.c_int]
     lib.orc_norm.restype = ctypes.c_double
     lib.orc_rel_error.argtypes = [ctypes.c_uint32, _i64p, _f64p, _i64p, _f64p, _i64p]
@@ -278,6 +284,58 @@ def entrywise(op, n, A, wA, B=None, wB=None, alpha=1.0, C=None, wC=None, offA=0,
                                _ptr(Cbuf, ctypes.c_double), _ptr(wC_, ctypes.c_int64))
     _check(rc, "entrywise")
     return Cbuf
+
+
+def transpose(A, nA, wA, tau, C=None, wC=None, offA=0):
+    """C = A^tau (Table 3, transpose): C(i^c) = A(i^a) with i^c_r = i^a_{tau_r}
+    and n^c_r = n^a_{tau_r}.  Returns (FP64 buffer of C, C's extents)."""
+    nA_ = _i64(nA)
+    p = len(nA_)
+    tau_ = _u32(tau)
+    nc = tuple(int(nA_[int(t) - 1]) for t in tau_)
+    wC_ = _i64(strides(nc) if wC is None else wC)
+    Cbuf = np.zeros(max(_span(nc, wC_), 1)) if C is None else _f64buf(C).copy()
+    Ab, wA_ = _f64buf(A), _i64(wA)
+    rc = _load().orc_transpose(p, _ptr(nA_, ctypes.c_int64), _ptr(Ab, ctypes.c_double, offA),
+                               _ptr(wA_, ctypes.c_int64), _ptr(tau_, ctypes.c_uint32),
+                               _ptr(Cbuf, ctypes.c_double), _ptr(wC_, ctypes.c_int64))
+    _check(rc, "transpose")
+    return Cbuf, nc
+
+
+def ttt_shape(nA, nB, q, phi, psi):
+    """Output extents of the (q, phi, psi)-mode product (Sec. 5.2)."""
+    r, s = len(nA) - q, len(nB) - q
+    return tuple(int(nA[phi[k] - 1]) for k in range(r)) + \
+        tuple(int(nB[psi[k] - 1]) for k in range(s))
+
+
+def ttt(A, nA, wA, phi, B, nB, wB, psi, q, C=None, wC=None, accumulate=False,
+        compensated=False, offA=0, offB=0):
+    """(q, phi, psi)-mode tensor-tensor multiplication (Sec. 5.2) in FP64.
+    phi / psi are 1-based; their first r / s entries order C's modes and
+    their last q entries pair the contracted modes.  Returns (FP64 buffer of
+    C, C's extents); an order-0 result is a one-element buffer."""
+    nA_, nB_ = _i64(nA), _i64(nB)
+    q = int(q)
+    r, s = len(nA_) - q, len(nB_) - q
+    if r < 0 or s < 0 or len(phi) != len(nA_) or len(psi) != len(nB_):
+        raise ValueError("phi / psi must have q+r / q+s entries")
+    nc = ttt_shape(nA_, nB_, q, list(phi), list(psi))
+    wC_ = _i64((strides(nc) if nc else ()) if wC is None else wC)
+    Cbuf = np.zeros(max(_span(nc, wC_) if nc else 1, 1)) if C is None else _f64buf(C).copy()
+    Ab, Bb = _f64buf(A), _f64buf(B)
+    wA_, wB_ = _i64(wA), _i64(wB)
+    phi_, psi_ = _u32(phi), _u32(psi)
+    rc = _load().orc_ttt(q, r, s, _ptr(nA_, ctypes.c_int64), _ptr(Ab, ctypes.c_double, offA),
+                         _ptr(wA_, ctypes.c_int64), _ptr(phi_, ctypes.c_uint32),
+                         _ptr(nB_, ctypes.c_int64), _ptr(Bb, ctypes.c_double, offB),
+                         _ptr(wB_, ctypes.c_int64), _ptr(psi_, ctypes.c_uint32),
+                         _ptr(Cbuf, ctypes.c_double),
+                         _ptr(wC_ if len(wC_) else _i64([0]), ctypes.c_int64),
+                         int(accumulate), int(compensated))
+    _check(rc, "ttt")
+    return Cbuf, nc
 
 
 def norm(A, n, wA, compensated=True, offA=0) -> float:

@@ -316,6 +316,84 @@ int orc_entrywise(int op, uint32_t p, const int64_t* n,
 }
 
 /* ---------------------------------------------------------------------- */
+/* Transposition: Table 3 (transpose)                                      */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * C(i^c_1..i^c_p) = A(i^a_1..i^a_p) with i^c_r = i^a_{tau_r}, hence
+ * n^c_r = n^a_{tau_r}; tau is a 1-based permutation of 1..p.  The odometer
+ * walks C's multi-index; A's index is assembled from it by i^a_{tau_r} =
+ * i^c_r.  wC has p entries (strides of C's modes).
+ */
+int orc_transpose(uint32_t p, const int64_t* nA, const double* A, const int64_t* wA,
+                  const uint32_t* tau, double* C, const int64_t* wC)
+{
+    int64_t nc[ORC_MAX_ORDER], ic[ORC_MAX_ORDER] = {0}, ia[ORC_MAX_ORDER];
+    if (p < 1 || p > ORC_MAX_ORDER || !is_permutation(p, tau)) return -1;
+    for (uint32_t r = 0; r < p; ++r) nc[r] = nA[tau[r] - 1];
+    if (any_zero(p, nc)) return 0;
+    do {
+        for (uint32_t r = 0; r < p; ++r) ia[tau[r] - 1] = ic[r];
+        C[orc_lambda(p, wC, ic, NULL)] = A[orc_lambda(p, wA, ia, NULL)];
+    } while (odometer_next(p, nc, ic));
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Tensor-tensor multiplication: Sec. 5.2, (q, phi, psi)-mode product      */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * A has order q+r, B order q+s, C order r+s; phi (q+r entries) and psi
+ * (q+s entries) are 1-based permutations.  With i^c the output index and
+ * j the contraction index (q entries):
+ *   i^a_{phi_k}     = i^c_k       (k = 1..r),   i^b_{psi_k}     = i^c_{r+k} (k = 1..s),
+ *   i^a_{phi_{r+k}} = j_k         (k = 1..q),   i^b_{psi_{s+k}} = j_k       (k = 1..q),
+ *   C(i^c) = sum_j A(i^a) * B(i^b),
+ * and the extents must satisfy n^a_{phi_{r+k}} = n^b_{psi_{s+k}}.  q = 0 is
+ * the outer product, r = s = 0 the inner product (C holds one element and
+ * wC is not read).  The contraction index is walked by the odometer (first
+ * contracted index fastest); accumulate and compensated as for ttv.
+ */
+int orc_ttt(uint32_t q, uint32_t r, uint32_t s,
+            const int64_t* nA, const double* A, const int64_t* wA, const uint32_t* phi,
+            const int64_t* nB, const double* B, const int64_t* wB, const uint32_t* psi,
+            double* C, const int64_t* wC, int accumulate, int compensated)
+{
+    int64_t nc[ORC_MAX_ORDER], nj[ORC_MAX_ORDER];
+    int64_t ic[ORC_MAX_ORDER] = {0}, j[ORC_MAX_ORDER], ia[ORC_MAX_ORDER], ib[ORC_MAX_ORDER];
+    const uint32_t pa = q + r, pb = q + s, pc = r + s;
+    if (pa < 1 || pb < 1 || pa > ORC_MAX_ORDER || pb > ORC_MAX_ORDER) return -1;
+    if (!is_permutation(pa, phi) || !is_permutation(pb, psi)) return -1;
+    for (uint32_t k = 0; k < q; ++k) {
+        nj[k] = nA[phi[r + k] - 1];
+        if (nB[psi[s + k] - 1] != nj[k]) return -2;
+    }
+    for (uint32_t k = 0; k < r; ++k) nc[k] = nA[phi[k] - 1];
+    for (uint32_t k = 0; k < s; ++k) nc[r + k] = nB[psi[k] - 1];
+    if (any_zero(pc, nc)) return 0;
+    do {
+        const int64_t co = pc ? orc_lambda(pc, wC, ic, NULL) : 0;
+        acc_t acc;
+        acc_init(&acc, accumulate ? C[co] : 0.0, compensated);
+        for (uint32_t k = 0; k < r; ++k) ia[phi[k] - 1] = ic[k];
+        for (uint32_t k = 0; k < s; ++k) ib[psi[k] - 1] = ic[r + k];
+        if (!any_zero(q, nj)) {
+            for (uint32_t k = 0; k < q; ++k) j[k] = 0;
+            do {
+                for (uint32_t k = 0; k < q; ++k) {
+                    ia[phi[r + k] - 1] = j[k];
+                    ib[psi[s + k] - 1] = j[k];
+                }
+                acc_add(&acc, A[orc_lambda(pa, wA, ia, NULL)] * B[orc_lambda(pb, wB, ib, NULL)]);
+            } while (q > 0 && odometer_next(q, nj, j));
+        }
+        C[co] = acc_get(&acc);
+    } while (pc > 0 && odometer_next(pc, nc, ic));
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Frobenius norm: Table 3 (norm)                                          */
 /* ---------------------------------------------------------------------- */
 
@@ -354,4 +432,4 @@ double orc_rel_error(uint32_t p, const int64_t* n, const double* A, const int64_
 }
 
 /* Version tag so a stale build is detectable. */
-int orc_version(void) { return 1; }
+int orc_version(void) { return 2; }

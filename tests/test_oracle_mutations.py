@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_ttt as pins_ttt
 
 MUTATIONS = {
     "stride_index_transposed": ("w[pi[r] - 1] = prod;", "w[r] = prod;"),
@@ -31,26 +32,39 @@ MUTATIONS = {
                                 "C[orc_lambda(p, wA, idx, NULL)] = apply_op"),
     "norm_abs_not_square": ("acc_add(&s, a * a);", "acc_add(&s, a < 0 ? -a : a);"),
     "ttv_output_mode_order": ("ext[c++] = n[r];", "ext[p - 2 - c++] = n[r];"),
+    "transpose_inverse_permutation": ("ia[tau[r] - 1] = ic[r];", "ia[r] = ic[tau[r] - 1];"),
+    "ttt_contraction_pairs_reversed": ("ib[psi[s + k] - 1] = j[k];",
+                                       "ib[psi[s + k] - 1] = j[q - 1 - k];"),
+    "ttt_b_free_index_from_a_block": ("ib[psi[k] - 1] = ic[r + k];", "ib[psi[k] - 1] = ic[k];"),
+    "ttt_last_contracted_term_dropped": ("} while (q > 0 && odometer_next(q, nj, j));",
+                                         "} while (q > 0 && odometer_next(q, nj, j) && "
+                                         "j[q - 1] + 1 < nj[q - 1]);"),
 }
 
-PINS = [getattr(pins, name) for name in dir(pins) if name.startswith("test_")]
+PINS = [getattr(mod, name) for mod in (pins, pins_ttt) for name in dir(mod)
+        if name.startswith("test_")]
+
+
+def _param_sets(fn):
+    """Argument sets of a pytest-parametrized pin (one dict per case)."""
+    sets = [{}]
+    for mark in getattr(fn, "pytestmark", []):
+        if mark.name != "parametrize":
+            continue
+        names = [x.strip() for x in mark.args[0].split(",")]
+        vals = [v if len(names) > 1 else (v,) for v in mark.args[1]]
+        sets = [dict(base, **dict(zip(names, v))) for base in sets for v in vals]
+    return sets
 
 
 def _run_pins():
-    """Runs every pin (parametrised ones with a few seeds); returns the names
-    of those that failed."""
+    """Runs every pin (a parametrised one over its cases, at most four seeds);
+    returns the names of those that failed."""
     failed = []
-    import inspect
     for fn in PINS:
-        params = inspect.signature(fn).parameters
-        if "op" in params:
-            argsets = [{"op": op} for op in range(6)]
-        elif "seed" in params:
-            argsets = [{"seed": s} for s in range(4)]
-        elif "p" in params:
-            argsets = [{"p": p} for p in (2, 3, 4)]
-        else:
-            argsets = [{}]
+        argsets = _param_sets(fn)
+        if argsets and set(argsets[0]) == {"seed"}:
+            argsets = argsets[:4]
         for kw in argsets:
             try:
                 fn(**kw)
