@@ -198,6 +198,36 @@ int tl_ttms(const tl_tensor* A, const void* const* mats, const int64_t* J, const
 int tl_hopm(const tl_tensor* A, void* const* u, double* lambda, uint32_t K, void* stream);
 
 /*
+ * tl_transpose -- C = A^tau (Table 3, transpose): C(i^c) = A(i^a) with
+ * i^c_r = i^a_{tau_r}, so C's extents are n^c_r = n^a_{tau_r}.  tau: p
+ * 1-based entries, a permutation.  C: any layout or strides.  Runs as an
+ * entrywise copy from A described in C's mode order (tiled transpose when
+ * the fastest modes differ).  Errors: TL_EINVAL (tau not a permutation, C's
+ * order or extents), as tl_entrywise otherwise.
+ */
+int tl_transpose(const tl_tensor* A, const uint32_t* tau, const tl_tensor* C, void* stream);
+
+/*
+ * tl_ttt -- the (q, phi, psi)-mode tensor-tensor product of Sec. 5.2:
+ * A of order q+r, B of order q+s, C of order r+s,
+ *   C(i^c) = sum over the q contraction indices j of A(i^a) * B(i^b),
+ *   i^a_{phi_k} = i^c_k (k <= r),  i^b_{psi_k} = i^c_{r+k} (k <= s),
+ *   i^a_{phi_{r+k}} = i^b_{psi_{s+k}} = j_k (k <= q),
+ * phi (q+r entries) and psi (q+s entries) 1-based permutations, with
+ * n^a_{phi_{r+k}} = n^b_{psi_{s+k}}.  q = 0 is the outer product; r = s = 0
+ * the inner product, whose C is one element (C->p = 0, or p = 1 with n = 1).
+ * precision as tl_ttm (the tensor-core precisions apply when the product
+ * runs as a ttm); accumulate != 0 adds to C.  Runs as one mode-1 ttv / ttm
+ * over re-described operands; operands whose strides do not allow that are
+ * first copied to dense layouts in per-stream workspace slots of the library,
+ * and C is written through a dense temporary when its strides do not allow
+ * it.  C must not overlap A or B.  Errors: TL_EINVAL (permutations, extents,
+ * C's shape), TL_EUNSUPPORTED (precision vs dtype), TL_ENOMEM, TL_ECUDA.
+ */
+int tl_ttt(const tl_tensor* A, const uint32_t* phi, const tl_tensor* B, const uint32_t* psi,
+           uint32_t q, const tl_tensor* C, int32_t precision, int32_t accumulate, void* stream);
+
+/*
  * tl_norm -- Frobenius norm ||A||_F = sqrt(sum_i A(i)^2) (Table 3, norm),
  * accumulated in FP64 with a deterministic two-pass block reduction.
  * result: device pointer to three doubles, written asynchronously:

@@ -187,6 +187,10 @@ def _declare(_lib):
     _lib.tl_ttms.argtypes = [_T, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64),
                              ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32, _T, ctypes.c_int32,
                              ctypes.c_void_p]
+    _lib.tl_transpose.argtypes = [_T, ctypes.POINTER(ctypes.c_uint32), _T, ctypes.c_void_p]
+    _lib.tl_ttt.argtypes = [_T, ctypes.POINTER(ctypes.c_uint32), _T,
+                            ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32, _T, ctypes.c_int32,
+                            ctypes.c_int32, ctypes.c_void_p]
     _lib.tl_hopm.argtypes = [_T, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_uint32,
                              ctypes.c_void_p]
 
@@ -253,6 +257,20 @@ def tl_ttms(A: Desc, mats, J, modes, C: Desc, precision: int = TL_P_DEFAULT, str
 
 def tl_hopm(A: Desc, u, lam, K: int, stream=None) -> int:
     return _lib.tl_hopm(A.ref, _ptr_array(u), _addr(lam), int(K), _stream(stream))
+
+
+def _u32_array(xs):
+    return (ctypes.c_uint32 * max(len(xs), 1))(*[int(x) for x in xs])
+
+
+def tl_transpose(A: Desc, tau, C: Desc, stream=None) -> int:
+    return _lib.tl_transpose(A.ref, _u32_array(tau), C.ref, _stream(stream))
+
+
+def tl_ttt(A: Desc, phi, B: Desc, psi, q: int, C: Desc, precision: int = TL_P_DEFAULT,
+           accumulate: int = 0, stream=None) -> int:
+    return _lib.tl_ttt(A.ref, _u32_array(phi), B.ref, _u32_array(psi), int(q), C.ref,
+                       int(precision), int(accumulate), _stream(stream))
 
 
 def tl_norm(A: Desc, result, stream=None) -> int:
