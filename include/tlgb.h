@@ -273,6 +273,20 @@ int tl_device_status(void* stream);
 int tl_selftest_wait_timeout(double limit_us, void* stream);
 
 /*
+ * tl_view -- host-only: the descriptor of a view of A (Sec. 3.3): for every
+ * mode r a range with first index f[r], step t[r] and last index l[r]
+ * (inclusive), 0 <= f[r] <= l[r] < n_r and t[r] >= 1.  The view has extents
+ * n'_r = (l_r - f_r) / t_r + 1 (Eq. 5), strides w'_r = w_r * t_r (Eq. 19,
+ * with w the strides of the tensor the view refers to, so views of views
+ * compose) and its first element at offset gamma = sum_r f_r w_r (Eq. 18).
+ * Writes V = {A->p, A->dtype, n_out, NULL, w_out, A->data + gamma elements};
+ * n_out and w_out are caller arrays of p entries that V points into.  Only
+ * pointer arithmetic: the data are not touched.  Errors: TL_EINVAL.
+ */
+int tl_view(const tl_tensor* A, const int64_t* f, const int64_t* t, const int64_t* l,
+            tl_tensor* V, int64_t* n_out, int64_t* w_out);
+
+/*
  * tl_plan_describe -- host-only: validates the arguments of a ttv (op 0),
  * ttm (op 1) or entrywise (op 2) call exactly as the entry point would and
  * writes a one-line JSON description of the collapsed iteration space and

@@ -191,6 +191,7 @@ def _declare(_lib):
     _lib.tl_ttt.argtypes = [_T, ctypes.POINTER(ctypes.c_uint32), _T,
                             ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32, _T, ctypes.c_int32,
                             ctypes.c_int32, ctypes.c_void_p]
+    _lib.tl_view.argtypes = [_T, _i64p, _i64p, _i64p, _T, _i64p, _i64p]
     _lib.tl_hopm.argtypes = [_T, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_uint32,
                              ctypes.c_void_p]
 
@@ -279,6 +280,21 @@ def tl_norm(A: Desc, result, stream=None) -> int:
 
 def tl_rel_error(X: Desc, R: Desc, result, stream=None) -> int:
     return _lib.tl_rel_error(X.ref, R.ref, _addr(result), _stream(stream))
+
+
+def tl_view(A: Desc, f, t, l):
+    """Descriptor of the view (f, t, l) of A (Sec. 3.3); returns (code, Desc)."""
+    p = len(A.n)
+    fa, ta, la = (ctypes.c_int64 * p)(*f), (ctypes.c_int64 * p)(*t), (ctypes.c_int64 * p)(*l)
+    nv, wv = (ctypes.c_int64 * p)(), (ctypes.c_int64 * p)()
+    V = tl_tensor()
+    rc = _lib.tl_view(A.ref, fa, ta, la, ctypes.byref(V), nv, wv)
+    if rc != TL_OK:
+        return rc, None
+    D = Desc(int(V.data or 0), tuple(nv), w=tuple(wv),
+             dtype="f64" if V.dtype == TL_F64 else "f32")
+    D._keep = getattr(A, "_keep", None)
+    return rc, D
 
 
 def tl_plan_describe(op: int, A: Desc, B, q: int, J: int, precision: int, entry_op: int,

@@ -332,6 +332,30 @@ static void append_space(std::string& s, const Space& sp)
     s += "]";
 }
 
+int tl_view(const tl_tensor* A_, const int64_t* f, const int64_t* t, const int64_t* l,
+            tl_tensor* V, int64_t* n_out, int64_t* w_out)
+{
+    Tensor A;
+    int rc = load_tensor(A_, false, A);
+    if (rc) return rc;
+    if (!f || !t || !l || !V || !n_out || !w_out) return TL_EINVAL;
+    int64_t gamma = 0;
+    for (uint32_t r = 0; r < A.p; ++r)
+        if (t[r] < 1 || f[r] < 0 || f[r] > l[r] || l[r] >= A.n[r]) return TL_EINVAL;
+    for (uint32_t r = 0; r < A.p; ++r) {
+        n_out[r] = (l[r] - f[r]) / t[r] + 1;
+        w_out[r] = A.w[r] * t[r];
+        gamma += f[r] * A.w[r];
+    }
+    V->p = A.p;
+    V->dtype = A.dtype;
+    V->n = n_out;
+    V->pi = nullptr;
+    V->w = w_out;
+    V->data = static_cast<char*>(A.data) + gamma * (int64_t)A.elem();
+    return TL_OK;
+}
+
 int tl_plan_describe(int32_t op, const tl_tensor* A_, const tl_tensor* B_, uint32_t q, int64_t J,
                      int32_t precision, int32_t entry_op, const tl_tensor* C_, char* buf,
                      size_t buflen)

@@ -165,3 +165,52 @@ def test_validation_errors(tl):
                  eop=tl.TL_ADD)[0] == 0
     assert _plan(tl, tl.TL_OP_ENTRYWISE, A, _desc(tl, n, (3, 2, 1)),
                  B=_desc(tl, n, addr=FAKE * 8192), eop=tl.TL_ADD)[0] == tl.TL_EINVAL
+
+
+# ------------------------------------------------------------------ views ---
+
+def test_view_descriptor_matches_the_oracle(tl):
+    # tl_view is pointer arithmetic only: the base address is never touched
+    g = synth.rng(77)
+    base = 1 << 40
+    for trial in range(40):
+        p = int(g.integers(1, 6))
+        n = tuple(int(g.integers(1, 12)) for _ in range(p))
+        pi = synth.random_layout(p, g)
+        w = oracle.strides(n, pi)
+        f = [int(g.integers(0, x)) for x in n]
+        l = [int(g.integers(a, x)) for a, x in zip(f, n)]
+        t = [int(g.integers(1, 4)) for _ in range(p)]
+        A = tl.Desc(base, n, pi, dtype="f64")
+        rc, V = tl.tl_view(A, f, t, l)
+        assert rc == tl.TL_OK
+        nv, wv, gamma = oracle.view(n, w, f, t, l)
+        assert V.n == nv and V.w == wv
+        assert V.s.data == base + 8 * gamma
+        # a view of the view composes (w'' = w' t, Eq. 19)
+        f2 = [0] * p
+        t2 = [2] * p
+        l2 = [x - 1 for x in nv]
+        rc, V2 = tl.tl_view(V, f2, t2, l2)
+        assert rc == tl.TL_OK
+        nv2, wv2, g2 = oracle.view(nv, wv, f2, t2, l2)
+        assert V2.n == nv2 and V2.w == wv2 and V2.s.data == V.s.data + 8 * g2
+
+
+def test_view_paper_example(tl):
+    # Sec. 3.3: A of shape (4, 2, 3) first-order; f = (1, 0, 2), t = (2, 1, 1),
+    # l = (3, 1, 2) gives n' = (2, 2, 1) and A'(0,0,0) = A(1,0,2)
+    A = tl.Desc(4096, (4, 2, 3), dtype="f32")
+    rc, V = tl.tl_view(A, (1, 0, 2), (2, 1, 1), (3, 1, 2))
+    assert rc == tl.TL_OK and V.n == (2, 2, 1)
+    w = oracle.strides((4, 2, 3))
+    assert V.s.data == 4096 + 4 * oracle.lam(w, (1, 0, 2))
+    # A'(1,1,0) = A(3,1,2)
+    assert (V.s.data - 4096) // 4 + oracle.lam(V.w, (1, 1, 0)) == oracle.lam(w, (3, 1, 2))
+
+
+def test_view_rejects_bad_ranges(tl):
+    A = tl.Desc(4096, (4, 2, 3), dtype="f32")
+    assert tl.tl_view(A, (0, 0, 0), (0, 1, 1), (3, 1, 2))[0] == tl.TL_EINVAL   # t < 1
+    assert tl.tl_view(A, (2, 0, 0), (1, 1, 1), (1, 1, 2))[0] == tl.TL_EINVAL   # f > l
+    assert tl.tl_view(A, (0, 0, 0), (1, 1, 1), (4, 1, 2))[0] == tl.TL_EINVAL   # l >= n
