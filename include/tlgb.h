@@ -208,7 +208,7 @@ int tl_hopm(const tl_tensor* A, void* const* u, double* lambda, uint32_t K, void
 int tl_transpose(const tl_tensor* A, const uint32_t* tau, const tl_tensor* C, void* stream);
 
 /*
- * tl_ttt -- the (q, phi, psi)-mode tensor-tensor product of Sec. 5.2:
+ * tl_ttt -- the (q, phi, psi)-mode tensor-tensor product of Sec. 5.2 (Eqs. 26-27):
  * A of order q+r, B of order q+s, C of order r+s,
  *   C(i^c) = sum over the q contraction indices j of A(i^a) * B(i^b),
  *   i^a_{phi_k} = i^c_k (k <= r),  i^b_{psi_k} = i^c_{r+k} (k <= s),

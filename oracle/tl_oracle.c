@@ -340,7 +340,7 @@ int orc_transpose(uint32_t p, const int64_t* nA, const double* A, const int64_t*
 }
 
 /* ---------------------------------------------------------------------- */
-/* Tensor-tensor multiplication: Sec. 5.2, (q, phi, psi)-mode product      */
+/* Tensor-tensor multiplication: Sec. 5.2 Eqs. 26-27 ((q, phi, psi)-mode)   */
 /* ---------------------------------------------------------------------- */
 
 /*

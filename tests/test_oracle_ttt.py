@@ -219,3 +219,17 @@ def test_ttt_integer_inputs_exact():
     mb, wb = _mem(Y, synth.random_layout(len(nB), g))
     buf, nc = oracle.ttt(ma, nA, wa, phi, mb, nB, wb, psi, 2)
     np.testing.assert_array_equal(buf.reshape(nc, order="F"), _einsum_ttt(X, Y, 2, phi, psi))
+
+
+def test_ttt_times_tensor_example_shapes():
+    # Sec. 5.2 member-function example: A {3,4,2,6} times C {2,3,4}, contracting
+    # A's modes 2, 3 with C's modes 3, 1, leaves A's modes 1, 4 then C's mode 2:
+    # in (q, phi, psi) form q = 2, phi = (1,4,2,3), psi = (2,3,1) -> {3,6,3}
+    nA, nC = (3, 4, 2, 6), (2, 3, 4)
+    X, Y = synth.uniform(nA, 58), synth.uniform(nC, 59)
+    ma, wa = _mem(X, (1, 2, 3, 4))
+    mc, wc = _mem(Y, (1, 2, 3))
+    buf, nd = oracle.ttt(ma, nA, wa, (1, 4, 2, 3), mc, nC, wc, (2, 3, 1), 2)
+    assert nd == (3, 6, 3)
+    ref = np.einsum("ijkl,kmj->ilm", X, Y)
+    assert np.allclose(buf.reshape(nd, order="F"), ref, rtol=1e-13)
