@@ -63,6 +63,8 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip the sequences / transpose / ttt / view measurements")
     ap.add_argument("--batch-ops", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--serve-rates", default="2000,10000,40000")
@@ -502,6 +504,9 @@ def main():
         if not args.no_precision:
             extras["precision"] = measure_precision(tl, torch, dev, sh)
             torch.cuda.empty_cache()
+        if not args.no_next:
+            extras["next"] = measure_next(tl, torch, dev, sh, edge, peaks)
+            torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -803,6 +808,109 @@ def measure_precision(tl, torch, dev, sh, edge=512, rank=64, samples=3000):
                      "TFLOP/s": round(tucker_flops / (t_ms / 1e3) / 1e12, 2),
                      "step_rel_frob_err": steps}
     return res
+
+
+def _time_ms(torch, fn, reps=5):
+    """Mean CUDA-event time of fn() over reps calls after one warm-up call."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_next(tl, torch, dev, sh, edge, peaks):
+    """The operations beyond single ttv / ttm / entrywise calls, each against
+    its roofline: transposition of the 128^4 tensor (HBM), ttv on a strided
+    view of it (HBM, bytes of the elements touched), the higher-order power
+    method on it (HBM: every ttv chain reads A once), the all-modes Tucker
+    projection of the 512^3 precision tensor in one tl_ttms call, and two
+    GEMM-shaped (q, phi, psi) contractions in split-BF16x3 (tensor pipe at
+    three MMAs per product), one direct and one that needs its matrix
+    operand packed."""
+    import synth
+    hbm = peaks["hbm_gbs"]
+    bf16 = peaks["bf16_tflops"]
+    out = {}
+    n = (edge,) * 4
+    N = edge ** 4
+    A = synth.device_normal(torch, N, 5151, torch.float32, dev)
+    DA = tl.Desc(A, n)
+    C = torch.empty(N, dtype=torch.float32, device=dev)
+    tr = []
+    for tau in ((2, 1, 3, 4), (1, 3, 2, 4), (4, 3, 2, 1), (2, 3, 4, 1)):
+        nc = tuple(n[t - 1] for t in tau)
+        ms = _time_ms(torch, lambda: tl.check(tl.tl_transpose(DA, tau, tl.Desc(C, nc), sh)))
+        gbs = 2 * N * 4 / (ms / 1e3) / 1e9
+        tr.append({"tau": list(tau), "ms": round(ms, 4), "GB/s": round(gbs, 1),
+                   "frac": round(gbs / hbm, 3)})
+    out["transpose"] = tr
+    # ttv along mode 2 of the view A[0:128:2, :, :, :] (every other row)
+    rc, V = tl.tl_view(DA, (0, 0, 0, 0), (2, 1, 1, 1), (edge - 2, edge - 1, edge - 1, edge - 1))
+    tl.check(rc)
+    b = synth.device_normal(torch, edge, 5152, torch.float32, dev)
+    nv = V.n
+    Cv = torch.empty(N // edge // 2, dtype=torch.float32, device=dev)
+    outn = (nv[0], nv[2], nv[3])
+    ms = _time_ms(torch, lambda: tl.check(tl.tl_ttv(V, b, 1, 2, tl.Desc(Cv, outn), 0, sh)))
+    touched = (N // 2 + N // 2 // edge) * 4
+    out["ttv_view_step2"] = {"ms": round(ms, 4), "GB/s_touched": round(touched / (ms / 1e3) / 1e9, 1),
+                             "note": "rows of 128 contiguous floats, every other one read"}
+    # HOPM: K sweeps, p ttv chains per sweep, each reading A once
+    us = [synth.device_normal(torch, edge, 5160 + r, torch.float32, dev) for r in range(4)]
+    for u in us:
+        u.div_(torch.linalg.vector_norm(u))
+    lam = torch.zeros(4, dtype=torch.float64, device=dev)
+    K = 3
+    ms = _time_ms(torch, lambda: tl.check(tl.tl_hopm(DA, us, lam, K, sh)), reps=2)
+    hopm_bytes = K * 4 * (N * 4)
+    gbs = hopm_bytes / (ms / 1e3) / 1e9
+    out["hopm"] = {"shape": list(n), "sweeps": K, "ms": round(ms, 3),
+                   "ms_per_sweep": round(ms / K, 3), "GB/s": round(gbs, 1),
+                   "frac": round(gbs / hbm, 3), "lambda": [float(x) for x in lam.cpu()]}
+    del A, C, Cv, us
+    torch.cuda.empty_cache()
+    # Tucker projection of the 512^3 precision tensor in one call
+    n3, mem, _, _, U = synth.precision_case()
+    A3 = torch.from_numpy(mem).to(dev)
+    Ud = [torch.from_numpy(np.ascontiguousarray(u).reshape(-1)).to(dev) for u in U]
+    rank = U[0].shape[0]
+    Ct = torch.empty(rank ** 3, dtype=torch.float32, device=dev)
+    ms = _time_ms(torch, lambda: tl.check(tl.tl_ttms(tl.Desc(A3, n3), Ud, (rank,) * 3, (1, 2, 3),
+                                                     tl.Desc(Ct, (rank,) * 3), tl.TL_P_BF16X3,
+                                                     sh)))
+    e = n3[0]
+    flops = 2 * rank * e ** 3 + 2 * rank * rank * e ** 2 + 2 * rank ** 3 * e
+    byts = (e ** 3 + 2 * rank * e * e + 2 * rank * rank * e + rank ** 3) * 4
+    out["ttms_tucker_512"] = {"ms": round(ms, 4), "TFLOP/s": round(flops / (ms / 1e3) / 1e12, 2),
+                              "GB/s": round(byts / (ms / 1e3) / 1e9, 1),
+                              "frac_hbm": round(byts / (ms / 1e3) / 1e9 / hbm, 3)}
+    del A3, Ct, Ud
+    torch.cuda.empty_cache()
+    # ttt: A (128,128,64,64) . B (64,64,512) over A's modes 3, 4 and B's 1, 2
+    nA, nB = (128, 128, 64, 64), (64, 64, 512)
+    At = synth.device_normal(torch, int(np.prod(nA)), 5170, torch.float32, dev)
+    Bt = synth.device_normal(torch, int(np.prod(nB)), 5171, torch.float32, dev)
+    nC = (128, 128, 512)
+    Cc = torch.empty(int(np.prod(nC)), dtype=torch.float32, device=dev)
+    flops = 2 * 128 * 128 * 512 * 64 * 64
+    tt = []
+    for name, pb, psi in (("direct", (1, 2, 3), (3, 1, 2)), ("packed_b", (3, 2, 1), (3, 1, 2))):
+        DB = tl.Desc(Bt, nB, pb)
+        ms = _time_ms(torch, lambda: tl.check(tl.tl_ttt(tl.Desc(At, nA), (1, 2, 3, 4), DB, psi,
+                                                        2, tl.Desc(Cc, nC), tl.TL_P_BF16X3, 0,
+                                                        sh)))
+        tf = flops / (ms / 1e3) / 1e12
+        tt.append({"route": name, "ms": round(ms, 4), "TFLOP/s": round(tf, 1),
+                   "frac_tensor_x3": round(3 * tf / bf16, 3)})
+    out["ttt_bf16x3"] = {"A": list(nA), "B": list(nB), "C": list(nC),
+                         "note": "frac_tensor_x3 = 3 MMAs per product / measured BF16 peak",
+                         "runs": tt}
+    return out
 
 
 def measure_e2e(tl, torch, wl, args, sh, world, barrier):

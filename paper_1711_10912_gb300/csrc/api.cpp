@@ -203,8 +203,9 @@ int tl_device_status(void* stream)
     if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return TL_ECUDA;
     int a = ttm_tc_status(true);
     int b = ttv_status(true);
-    if (a == TL_ECUDA || b == TL_ECUDA) return TL_ECUDA;
-    return (a == TL_ETIMEOUT || b == TL_ETIMEOUT) ? TL_ETIMEOUT : TL_OK;
+    int c = ew_status(true);
+    if (a == TL_ECUDA || b == TL_ECUDA || c == TL_ECUDA) return TL_ECUDA;
+    return (a == TL_ETIMEOUT || b == TL_ETIMEOUT || c == TL_ETIMEOUT) ? TL_ETIMEOUT : TL_OK;
 }
 
 const char* tl_strerror(int code)

@@ -15,6 +15,8 @@
 //   ew_rows     every operand is contiguous along dim 0 but the other dims
 //               are ordered differently: one offset decode per 16-byte vector.
 //   ew_generic  anything else: each element's offsets come from the mapper.
+// FP32 cases of ew_tile and ew_rows that a tensor map can describe run on the
+// TMA-staged kernel of ew_tma.cu instead.
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -113,9 +115,11 @@ __global__ void __launch_bounds__(kThreads) ew_generic_kernel(const EwArgs a)
 
 // All operands unit-stride along dim 0 but laid out differently in the other
 // dims: one offset decode per 16-byte vector along dim 0, vector loads and
-// stores (dim 0's extent and every other stride are multiples of VEC).
-template <typename T, int VEC>
-__global__ void __launch_bounds__(kThreads) ew_rows_kernel(const EwArgs a)
+// stores (dim 0's extent and every other stride are multiples of VEC).  Each
+// thread issues the loads of U vectors before their stores, so a resident
+// SM keeps enough bytes in flight to cover the HBM latency.
+template <typename T, int VEC, int U>
+__global__ void __launch_bounds__(kThreads, 4) ew_rows_kernel(const EwArgs a)
 {
     const T* __restrict__ A = static_cast<const T*>(a.A);
     const T* __restrict__ B = static_cast<const T*>(a.B);
@@ -124,7 +128,27 @@ __global__ void __launch_bounds__(kThreads) ew_rows_kernel(const EwArgs a)
     const bool unary = (a.op == TL_COPY || a.op == TL_SCALE);
     const int64_t nvec = a.N / VEC;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < nvec; g += stride) {
+    int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    for (; g + (U - 1) * stride < nvec; g += U * stride) {
+        int64_t off[U][3];
+        T x[U][VEC], y[U][VEC];
+#pragma unroll
+        for (int u = 0; u < U; ++u) map_offsets<3>(a.sp, g + u * stride, VEC, off[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            vload_stream<T, VEC>(A + off[u][0], x[u]);
+            if (!unary) vload_stream<T, VEC>(B + off[u][1], y[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            T r[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v)
+                r[v] = apply<T>(a.op, x[u][v], unary ? T(0) : y[u][v], alpha);
+            vstore<T, VEC>(C + off[u][2], r);
+        }
+    }
+    for (; g < nvec; g += stride) {
         int64_t off[3];
         map_offsets<3>(a.sp, g, VEC, off);
         T x[VEC], y[VEC], r[VEC];
@@ -335,7 +359,7 @@ int launch_typed(const EwPlan& P, const void* A, const void* B, double alpha, vo
         if (P.vec > 1) ew_tile_vec_kernel<T><<<grid, kThreads, 0, st>>>(a, tiles0, tiles1, batch);
         else ew_tile_kernel<T><<<grid, kThreads, 0, st>>>(a, tiles0, tiles1, batch);
     } else if (P.kernel == K_EW_ROWS) {
-        ew_rows_kernel<T, V><<<grid_for(P.N / V, num_sms), kThreads, 0, st>>>(a);
+        ew_rows_kernel<T, V, 2><<<grid_for((P.N / V + 1) / 2, num_sms), kThreads, 0, st>>>(a);
     } else {
         ew_generic_kernel<T><<<grid_for(P.N, num_sms), kThreads, 0, st>>>(a);
     }
@@ -348,6 +372,7 @@ int launch_entrywise(const EwPlan& P, const void* A, const void* B, double alpha
                      int num_sms, cudaStream_t st)
 {
     if (P.N == 0) return TL_OK;
+    if (P.kernel == K_EW_TMA) return launch_ew_tma(P, A, B, alpha, C, num_sms, st);
     if (P.dtype == TL_F64) return launch_typed<double>(P, A, B, alpha, C, num_sms, st);
     return launch_typed<float>(P, A, B, alpha, C, num_sms, st);
 }

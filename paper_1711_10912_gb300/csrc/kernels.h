@@ -15,6 +15,10 @@ int launch_ttv(const TtvPlan& P, const void* A, const void* b, void* C, void* ws
 
 int launch_entrywise(const EwPlan& P, const void* A, const void* B, double alpha, void* C,
                      int num_sms, cudaStream_t st);
+int launch_ew_tma(const EwPlan& P, const void* A, const void* B, double alpha, void* C,
+                  int num_sms, cudaStream_t st);
+// TL_ETIMEOUT if a bounded wait of the TMA entrywise kernel gave up.
+int ew_status(bool clear);
 
 int launch_ttm_simt(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate,
                     int num_sms, cudaStream_t st);

@@ -128,6 +128,7 @@ const char* kernel_name(int k)
     case K_EW_ROWS: return "ew_rows";
     case K_TTM_SIMT: return "ttm_simt";
     case K_TTM_TC: return "ttm_tc";
+    case K_EW_TMA: return "ew_tma";
     default: return "none";
     }
 }
@@ -330,6 +331,40 @@ int plan_entrywise(int32_t op, const Tensor& A, const Tensor* B, const Tensor& C
         if (v) {
             P.kernel = K_EW_ROWS;
             P.vec = V;
+        }
+    }
+    // FP32 tiles and permuted rows go through TMA-staged 32 x 32 tiles when
+    // every input is unit-stride along dim 0 or along the tiled dim t, C along
+    // dim 0, there are at most 5 dims (the tensor-map rank), every other
+    // stride is a multiple of 16 bytes and the bases are 16-byte aligned.
+    if (A.dtype == TL_F32 && (P.kernel == K_EW_TILE || P.kernel == K_EW_ROWS) && P.sp.nd >= 2 &&
+        P.sp.nd <= 5) {
+        const Space& sp = P.sp;
+        const int t = P.kernel == K_EW_TILE ? P.tdim : 1;
+        bool ok = sp.d[0].s[2] == 1 && aligned(A.data, 16) && aligned(C.data, 16) &&
+                  (!B || aligned(B->data, 16));
+        for (int o = 0; o < 3 && ok; ++o) {
+            if (o == 1 && !B) continue;
+            const int unit = sp.d[0].s[o] == 1 ? 0 : (o < 2 && sp.d[t].s[o] == 1 ? t : -1);
+            if (unit < 0) ok = false;
+            for (int d = 0; d < sp.nd && ok; ++d)
+                if (d != unit) ok = sp.d[d].s[o] % 4 == 0 && sp.d[d].s[o] < (int64_t(1) << 38);
+        }
+        for (int d = 0; d < sp.nd && ok; ++d) ok = sp.d[d].n < (int64_t(1) << 31);
+        // 32 x 32 tiles are numbered in 32-bit arithmetic
+        if (ok) {
+            int64_t tiles = ((sp.d[0].n + 31) / 32) * ((sp.d[t].n + 31) / 32);
+            for (int d = 1; d < sp.nd && ok; ++d)
+                if (d != t) {
+                    tiles *= sp.d[d].n;
+                    ok = tiles < (int64_t(1) << 31);
+                }
+            ok = ok && tiles < (int64_t(1) << 31);
+        }
+        if (ok) {
+            P.kernel = K_EW_TMA;
+            P.tdim = t;
+            P.vec = 4;
         }
     }
     return TL_OK;

@@ -79,6 +79,7 @@ enum Kernel : int {
     K_EW_ROWS,        // all contiguous along dim 0, other dims permuted: per-vector mapping
     K_TTM_SIMT,       // register-tiled FP32 / FP64 batched GEMM
     K_TTM_TC,         // tcgen05 tensor-core batched GEMM
+    K_EW_TMA,         // FP32, layouts differ, <= 5 dims: TMA-staged 32 x 32 tiles
 };
 
 const char* kernel_name(int k);

@@ -122,11 +122,24 @@ def test_collapse_preserves_element_triples_entrywise(tl, seed):
 def test_entrywise_kernel_choice(tl):
     n = (64, 64, 64)
     F, L = (1, 2, 3), (3, 2, 1)
-    for pa, pb, pc, kern in [(F, F, F, "ew_flat"), (F, L, F, "ew_tile"), (L, F, F, "ew_tile"),
-                             (L, L, L, "ew_flat")]:
-        rc, P = _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, n, pa), _desc(tl, n, pc, addr=FAKE * 4096),
-                      B=_desc(tl, n, pb, addr=FAKE * 8192), eop=tl.TL_ADD)
-        assert rc == 0 and P["kernel"] == kern
+    # FP32 mixed layouts a tensor map can describe take the TMA tile kernel;
+    # FP64 takes the register-tiled transpose
+    for dtype, tile in (("f32", "ew_tma"), ("f64", "ew_tile")):
+        for pa, pb, pc, kern in [(F, F, F, "ew_flat"), (F, L, F, tile), (L, F, F, tile),
+                                 (L, L, L, "ew_flat")]:
+            rc, P = _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, n, pa, dtype=dtype),
+                          _desc(tl, n, pc, dtype=dtype, addr=FAKE * 4096),
+                          B=_desc(tl, n, pb, dtype=dtype, addr=FAKE * 8192), eop=tl.TL_ADD)
+            assert rc == 0 and P["kernel"] == kern, (dtype, pa, pb, pc, P)
+    # FP32 but beyond the tensor-map rank (6 dims that do not collapse), or
+    # with strides that are not multiples of 16 bytes: the older kernels
+    n6 = (8, 3, 2, 3, 2, 4)
+    rc, P = _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, n6, (1, 2, 3, 4, 5, 6)),
+                  _desc(tl, n6, (1, 6, 5, 4, 3, 2), addr=FAKE * 4096), eop=tl.TL_COPY)
+    assert rc == 0 and P["kernel"] == "ew_rows", P
+    rc, P = _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, (5, 7, 3), (1, 2, 3)),
+                  _desc(tl, (5, 7, 3), (2, 1, 3), addr=FAKE * 4096), eop=tl.TL_COPY)
+    assert rc == 0 and P["kernel"] == "ew_tile", P
 
 
 def test_validation_errors(tl):

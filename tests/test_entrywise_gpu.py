@@ -122,7 +122,10 @@ def test_entrywise_vector_tile_path_is_taken(tl, cuda_dev):
         rc, js = tl.tl_plan_describe(tl.TL_OP_ENTRYWISE, tl.Desc(A, n, (1, 2, 3)),
                                      tl.Desc(B, n, (3, 2, 1)), 0, 0, 0, 0, tl.Desc(C, n))
         P = json.loads(js)
-        assert P["kernel"] == "ew_tile" and P["vec"] == (4 if dtype == "f32" else 2), P
+        if dtype == "f32":
+            assert P["kernel"] == "ew_tma", P
+        else:
+            assert P["kernel"] == "ew_tile" and P["vec"] == 2, P
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
@@ -138,6 +141,35 @@ def test_entrywise_shared_fastest_mode_rows_path(tl, cuda_dev, dtype):
         C = torch.empty_like(A)
         rc, js = tl.tl_plan_describe(tl.TL_OP_ENTRYWISE, tl.Desc(A, n, pa), tl.Desc(B, n, pb),
                                      0, 0, 0, tl.TL_MUL, tl.Desc(C, n, pc))
-        assert json.loads(js)["kernel"] == "ew_rows", js
+        assert json.loads(js)["kernel"] == ("ew_tma" if dtype == "f32" else "ew_rows"), js
         got, ref = ew_case(tl, cuda_dev, OPS["mul"], X, Y, pa, pb, pc, dtype)
         np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("shape", [(36, 20, 64), (8, 12, 16, 20), (64, 36, 4, 8, 12), (96, 33 * 4, 8),
+                                   (4, 4, 4, 4, 4)])
+@pytest.mark.parametrize("op", ["add", "div", "copy", "scale"])
+def test_entrywise_tma_tiles_bit_exact(tl, cuda_dev, shape, op):
+    # FP32 layouts whose strides are multiples of 16 bytes take the TMA-staged
+    # tile kernel: transposed and direct inputs, ragged tiles, up to 3 batch dims
+    import json
+    p = len(shape)
+    g = synth.rng(3600 + p)
+    X = synth.normal(shape, 3601, dtype=np.float64)
+    Y = synth.normal(shape, 3602, dtype=np.float64) + 3.0
+    F, L = synth.first_order(p), synth.last_order(p)
+    combos = [(F, L, F), (L, F, F), (L, L, F), (F, F, L), (synth.random_layout(p, g), F, F)]
+    seen = set()
+    for pa, pb, pc in combos:
+        A = put(X, pa, cuda_dev, "f32")
+        B = put(Y, pb, cuda_dev, "f32")
+        C = torch.empty_like(A)
+        unary = OPS[op] in (4, 5)
+        rc, js = tl.tl_plan_describe(tl.TL_OP_ENTRYWISE, tl.Desc(A, shape, pa),
+                                     None if unary else tl.Desc(B, shape, pb), 0, 0, 0, OPS[op],
+                                     tl.Desc(C, shape, pc))
+        assert rc == 0
+        seen.add(json.loads(js)["kernel"])
+        got, ref = ew_case(tl, cuda_dev, OPS[op], X, Y, pa, pb, pc, "f32")
+        np.testing.assert_array_equal(got, ref)
+    assert "ew_tma" in seen, seen
