@@ -1029,10 +1029,26 @@ def measure_e2e(tl, torch, wl, args, sh, world, barrier):
     ms = max_over_ranks(torch, s.elapsed_time(e), dev)
     # the last ttm output copied back equals the device-resident run's
     same = bool(torch.equal(oM, wl.Cm.cpu()))
+    # the host link's own copy rate (1 GiB each way, copy engine), the bound
+    # the device-to-host bytes of a step put on it
+    link = {}
+    for name, dst, src in (("d2h_GB/s", oM, outs[-1]), ("h2d_GB/s", sets[0]["AF"], hF)):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        dst.copy_(src, non_blocking=True)
+        t0.record(compute)
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        t1.record(compute)
+        torch.cuda.synchronize()
+        link[name] = round(3 * src.numel() * 4 / (t0.elapsed_time(t1) / 1e3) / 1e9, 1)
+    bound_ms = max(d2h / (link["d2h_GB/s"] * 1e9), h2d / (link["h2d_GB/s"] * 1e9)) * 1e3
+    link["bound_ms_per_step"] = round(bound_ms, 3)
+    link["frac"] = round(bound_ms / (ms / steps), 3)
     return {"value": round(job_throughput(wl.step_bytes, world, steps, ms), 2), "unit": "GB/s",
             "last_output_matches_device_run": same,
             "ms_per_step": round(ms / steps, 3), "steps": steps,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "link": link,
             "overlap": "inputs double-buffered on a copy stream; each output copied back on a "
                        "second copy stream as soon as its call ends"}
 
