@@ -46,6 +46,7 @@ enum : int32_t {
     BV_TTM_32 = 4,       // smem-tiled GEMM tile of 32 rows
     BV_TTM_64 = 5,       // 64 rows
     BV_EW = 6,           // one thread per element
+    BV_TTM_SMALL = 7,    // B in shared memory, a row per thread, J outputs in registers
 };
 
 struct BOp {
@@ -206,6 +207,77 @@ __device__ void unit_ttm(const BOp& op, int64_t m0, uint8_t* smem)
     __syncthreads();
 }
 
+// ttm with the whole J x n_q matrix in shared memory (n_q <= 64, J <= 64 for
+// FP32, J <= 32 for FP64): one row of A per thread, JB <= 32 of its outputs
+// kept in registers per pass (a second pass re-reads the row, from L1/L2, when
+// J > 32), k unrolled 8 deep so eight loads of A are in flight per thread, B
+// read as 16-byte broadcasts.
+template <typename T, int JB>
+__device__ void unit_ttm_small(const BOp& op, int64_t e0, int64_t e1, uint8_t* smem)
+{
+    constexpr int V = 16 / sizeof(T);
+    using VT = typename Vec<T, V>::type;
+    const T* A = static_cast<const T*>(op.A);
+    const T* B = static_cast<const T*>(op.B);
+    T* C = static_cast<T*>(op.C);
+    const int nq = (int)op.nq, J = (int)op.J;
+    const int JT = (J + JB - 1) / JB * JB;        // padded columns held in shared memory
+    T* Bs = reinterpret_cast<T*>(smem);           // [n_q][JT], zero beyond J
+    for (int e = threadIdx.x; e < nq * JT; e += kThreads) {
+        const int k = e / JT, j = e - k * JT;
+        Bs[e] = j < J ? __ldg(B + j * op.ldb_row + k * op.ldb_col) : T(0);
+    }
+    __syncthreads();
+    for (int64_t m = e0 + threadIdx.x; m < e1; m += kThreads) {
+        int64_t oa, oc, unused;
+        bdecode(op, m, oa, oc, unused);
+        const T* pa = A + oa;
+        T* pc = C + oc;
+        for (int j0 = 0; j0 < J; j0 += JB) {
+            T acc[JB];
+#pragma unroll
+            for (int j = 0; j < JB; ++j) acc[j] = T(0);
+            int k = 0;
+            for (; k + 8 <= nq; k += 8) {
+                T a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = __ldg(pa + (int64_t)(k + u) * op.saq);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const VT* brow = reinterpret_cast<const VT*>(Bs + (k + u) * JT + j0);
+#pragma unroll
+                    for (int j = 0; j < JB / V; ++j) {
+                        const VT bv = brow[j];
+                        const T* be = reinterpret_cast<const T*>(&bv);
+#pragma unroll
+                        for (int v = 0; v < V; ++v)
+                            acc[j * V + v] = fma(a[u], be[v], acc[j * V + v]);
+                    }
+                }
+            }
+            for (; k < nq; ++k) {
+                const T a = __ldg(pa + (int64_t)k * op.saq);
+                const VT* brow = reinterpret_cast<const VT*>(Bs + k * JT + j0);
+#pragma unroll
+                for (int j = 0; j < JB / V; ++j) {
+                    const VT bv = brow[j];
+                    const T* be = reinterpret_cast<const T*>(&bv);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[j * V + v] = fma(a, be[v], acc[j * V + v]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < JB; ++j) {
+                if (j0 + j < J) {
+                    T* p = pc + (int64_t)(j0 + j) * op.scq;
+                    *p = op.accumulate ? *p + acc[j] : acc[j];
+                }
+            }
+        }
+    }
+    __syncthreads();          // Bs is rewritten by the next unit
+}
+
 template <typename T>
 __device__ void unit_ew(const BOp& op, int64_t e0, int64_t e1)
 {
@@ -248,13 +320,19 @@ __device__ void run_unit(const BOp& op, int64_t u, uint8_t* smem)
     case BV_TTM_64:
         for (int64_t m0 = e0; m0 < e1; m0 += 64) unit_ttm<T, 64>(op, m0, smem);
         break;
+    case BV_TTM_SMALL:
+        if (op.J <= 4) unit_ttm_small<T, 4>(op, e0, e1, smem);
+        else if (op.J <= 8) unit_ttm_small<T, 8>(op, e0, e1, smem);
+        else if (op.J <= 16) unit_ttm_small<T, 16>(op, e0, e1, smem);
+        else unit_ttm_small<T, (sizeof(T) == 8 ? 16 : 32)>(op, e0, e1, smem);
+        break;
     default: unit_ew<T>(op, e0, e1); break;
     }
 }
 
 constexpr size_t kSmem = 8 * 16 * (64 + 1 + 64 + 1) + 2 * 64 * 8;   // FP64 ttm tile
 
-__global__ void __launch_bounds__(kThreads) batch_kernel(const BOp* __restrict__ ops, int nops,
+__global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BOp* __restrict__ ops, int nops,
                                                          int64_t total_units,
                                                          unsigned long long* counter)
 {
@@ -307,6 +385,13 @@ struct Candidate {
     int64_t unit;
 };
 
+// The shared-memory ttm unit takes B whole: n_q <= 64 and J <= 64 (FP32) or
+// 32 (FP64), so B fits the kernel's static shared memory.
+bool small_ttm_host(const BOp& op)
+{
+    return op.kind == TL_OP_TTM && op.nq <= 64 && op.J <= (op.dtype == TL_F64 ? 32 : 64);
+}
+
 std::string class_key(const BOp& op)
 {
     auto lg = [](int64_t x) { int b = 0; while ((int64_t(1) << b) < x) ++b; return b; };
@@ -329,6 +414,7 @@ std::vector<Candidate> candidates(const BOp& op)
         for (int64_t u : {256, 1024, 4096}) {
             c.push_back({BV_TTM_32, u});
             c.push_back({BV_TTM_64, u});
+            if (small_ttm_host(op)) c.push_back({BV_TTM_SMALL, u});
         }
     } else {
         for (int64_t u : {8192, 65536}) c.push_back({BV_EW, u});
@@ -343,7 +429,10 @@ Candidate heuristic(const BOp& op)
         if (op.saq == 1 && op.nq >= 32) return {BV_TTV_ROW8, 2048};
         return {BV_TTV_COL, 4096};
     }
-    if (op.kind == TL_OP_TTM) return op.count >= 4096 ? Candidate{BV_TTM_64, 1024} : Candidate{BV_TTM_32, 256};
+    if (op.kind == TL_OP_TTM) {
+        if (small_ttm_host(op)) return {BV_TTM_SMALL, 1024};
+        return op.count >= 4096 ? Candidate{BV_TTM_64, 1024} : Candidate{BV_TTM_32, 256};
+    }
     return {BV_EW, 65536};
 }
 
@@ -716,15 +805,16 @@ int batch_set_variant(Batch* B, int32_t kind, int32_t variant, int64_t unit, voi
     const bool ok_kind =
         (kind == TL_OP_TTV && (variant == BV_TTV_COL || variant == BV_TTV_ROW4 ||
                                variant == BV_TTV_ROW8 || variant == BV_TTV_ROW32)) ||
-        (kind == TL_OP_TTM && (variant == BV_TTM_32 || variant == BV_TTM_64)) ||
+        (kind == TL_OP_TTM &&
+         (variant == BV_TTM_32 || variant == BV_TTM_64 || variant == BV_TTM_SMALL)) ||
         (kind == TL_OP_ENTRYWISE && variant == BV_EW);
     if (!ok_kind) return TL_EINVAL;
-    if (kind == TL_OP_TTM) {          // a ttm unit is a whole number of row tiles
+    if (kind == TL_OP_TTM && variant != BV_TTM_SMALL) {   // whole row tiles
         const int64_t bm = variant == BV_TTM_32 ? 32 : 64;
         unit = (unit + bm - 1) / bm * bm;
     }
     for (BOp& b : B->host)
-        if (b.kind == kind) {
+        if (b.kind == kind && (variant != BV_TTM_SMALL || small_ttm_host(b))) {
             b.variant = variant;
             b.unit = unit;
         }
@@ -755,9 +845,9 @@ int batch_describe(const Batch* B, char* buf, size_t len)
     std::snprintf(buf, len,
                   "{\"ops\":%zu,\"direct\":%d,\"units\":%lld,\"grid\":%d,\"bytes\":%zu,"
                   "\"variants\":{\"ttv_col\":%d,\"ttv_row4\":%d,\"ttv_row8\":%d,\"ttv_row32\":%d,"
-                  "\"ttm32\":%d,\"ttm64\":%d,\"ew\":%d}}",
+                  "\"ttm32\":%d,\"ttm64\":%d,\"ew\":%d,\"ttm_small\":%d}}",
                   B->host.size(), B->direct, (long long)B->total_units, grid_size(), B->bytes,
-                  hist[0], hist[1], hist[2], hist[3], hist[4], hist[5], hist[6]);
+                  hist[0], hist[1], hist[2], hist[3], hist[4], hist[5], hist[6], hist[7]);
     return TL_OK;
 }
 

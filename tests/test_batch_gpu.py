@@ -127,7 +127,7 @@ def test_batch_every_ttv_variant(tl, cuda_dev, variant, unit):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-@pytest.mark.parametrize("variant", ["TTM_32", "TTM_64"])
+@pytest.mark.parametrize("variant", ["TTM_32", "TTM_64", "TTM_SMALL"])
 def test_batch_every_ttm_variant(tl, cuda_dev, dtype, variant):
     s = OpSet(tl, cuda_dev, 120, 7200, dtype)
     rc, b = tl.tl_batch_create(s.ops, 0)
