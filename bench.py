@@ -849,17 +849,23 @@ def measure_next(tl, torch, dev, sh, edge, peaks):
         tr.append({"tau": list(tau), "ms": round(ms, 4), "GB/s": round(gbs, 1),
                    "frac": round(gbs / hbm, 3)})
     out["transpose"] = tr
-    # ttv along mode 2 of the view A[0:128:2, :, :, :] (every other row)
-    rc, V = tl.tl_view(DA, (0, 0, 0, 0), (2, 1, 1, 1), (edge - 2, edge - 1, edge - 1, edge - 1))
-    tl.check(rc)
+    # ttv along mode 2 of two step-2 views: every other element of the
+    # contiguous mode 1 (each 32-byte sector half used, so DRAM moves twice
+    # the touched bytes), and every other index of mode 3 (whole rows skipped)
     b = synth.device_normal(torch, edge, 5152, torch.float32, dev)
-    nv = V.n
-    Cv = torch.empty(N // edge // 2, dtype=torch.float32, device=dev)
-    outn = (nv[0], nv[2], nv[3])
-    ms = _time_ms(torch, lambda: tl.check(tl.tl_ttv(V, b, 1, 2, tl.Desc(Cv, outn), 0, sh)))
-    touched = (N // 2 + N // 2 // edge) * 4
-    out["ttv_view_step2"] = {"ms": round(ms, 4), "GB/s_touched": round(touched / (ms / 1e3) / 1e9, 1),
-                             "note": "rows of 128 contiguous floats, every other one read"}
+    views = {}
+    for name, t in (("step2_mode1", (2, 1, 1, 1)), ("step2_mode3", (1, 1, 2, 1))):
+        last = tuple(edge - 1 - (edge - 1) % s for s in t)
+        rc, V = tl.tl_view(DA, (0, 0, 0, 0), t, last)
+        tl.check(rc)
+        nv = V.n
+        outn = (nv[0], nv[2], nv[3])
+        Cv = torch.empty(int(np.prod(outn)), dtype=torch.float32, device=dev)
+        ms = _time_ms(torch, lambda: tl.check(tl.tl_ttv(V, b, 1, 2, tl.Desc(Cv, outn), 0, sh)))
+        touched = (int(np.prod(nv)) + int(np.prod(outn)) + edge) * 4
+        views[name] = {"view_shape": list(nv), "ms": round(ms, 4),
+                       "GB/s_touched": round(touched / (ms / 1e3) / 1e9, 1)}
+    out["ttv_on_views"] = views
     # HOPM: K sweeps, p ttv chains per sweep, each reading A once
     us = [synth.device_normal(torch, edge, 5160 + r, torch.float32, dev) for r in range(4)]
     for u in us:
@@ -872,7 +878,7 @@ def measure_next(tl, torch, dev, sh, edge, peaks):
     out["hopm"] = {"shape": list(n), "sweeps": K, "ms": round(ms, 3),
                    "ms_per_sweep": round(ms / K, 3), "GB/s": round(gbs, 1),
                    "frac": round(gbs / hbm, 3), "lambda": [float(x) for x in lam.cpu()]}
-    del A, C, Cv, us
+    del A, C, us
     torch.cuda.empty_cache()
     # Tucker projection of the 512^3 precision tensor in one call
     n3, mem, _, _, U = synth.precision_case()
