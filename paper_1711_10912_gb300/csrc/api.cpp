@@ -172,13 +172,22 @@ int prepare_entrywise(int32_t op, const tl_tensor* A_, const tl_tensor* B_, cons
     return TL_OK;
 }
 
-int ttm_launches(const TtmPlan& P) { return P.kernel == K_TTM_TC ? ttm_tc_launches(P) : 1; }
+int ttm_launches(const TtmPlan& P)
+{
+    return P.kernel == K_TTM_TC ? ttm_tc_launches(P) : ttm_simt_launches(P, device_sms());
+}
 
 int run_ttm(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate, int sms,
             cudaStream_t st)
 {
     if (P.kernel == K_TTM_TC) return launch_ttm_tc(P, A, B, C, accumulate, sms, st);
-    return launch_ttm_simt(P, A, B, C, accumulate, sms, st);
+    void* ws = nullptr;
+    const size_t wsb = ttm_simt_workspace_bytes(P, sms);
+    if (wsb) {
+        ws = workspace(st, wsb);
+        if (!ws) return TL_ENOMEM;
+    }
+    return launch_ttm_simt(P, A, B, C, accumulate, ws, sms, st);
 }
 
 }  // namespace tl
@@ -385,12 +394,14 @@ int tl_plan_describe(int32_t op, const tl_tensor* A_, const tl_tensor* B_, uint3
         static const float dummy[1] = {0.f};
         rc = prepare_ttm(A_, dummy, J, 0, 0, q, C_, precision, A, C, P);
         if (rc) return rc;
+        const long long splits =
+            P.kernel == K_TTM_SIMT ? (long long)ttm_simt_splits(P, 152, nullptr) : 1;
         std::snprintf(b, sizeof b,
                       "{\"op\":\"ttm\",\"kernel\":\"%s\",\"precision\":%d,\"nq\":%lld,"
                       "\"saq\":%lld,\"J\":%lld,\"scq\":%lld,\"M\":%lld,\"tc_variant\":%d,"
-                      "\"dims\":",
+                      "\"splits\":%lld,\"dims\":",
                       kernel_name(P.kernel), P.precision, (long long)P.nq, (long long)P.saq,
-                      (long long)P.J, (long long)P.scq, (long long)P.M, P.tc_variant);
+                      (long long)P.J, (long long)P.scq, (long long)P.M, P.tc_variant, splits);
         s = b;
         append_space(s, P.rows);
         s += "}";

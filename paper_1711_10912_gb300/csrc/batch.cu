@@ -528,7 +528,8 @@ static int fill_op(const tl_op& o, BOp& b, size_t& bytes, bool& direct)
         TtvPlan P;
         int rc = prepare_ttv(&o.A, o.vec, o.incb, o.q, &o.C, sms, A, C, P);
         if (rc) return rc;
-        if (P.out.nd > kBD) { direct = true; return TL_OK; }
+        // a split k range (few outputs, long n_q) runs on the split-K kernels
+        if (P.out.nd > kBD || P.splits > 1) { direct = true; return TL_OK; }
         b.dtype = A.dtype;
         b.nd = P.out.nd;
         for (int d = 0; d < P.out.nd; ++d) {
@@ -549,7 +550,10 @@ static int fill_op(const tl_op& o, BOp& b, size_t& bytes, bool& direct)
         TtmPlan P;
         int rc = prepare_ttm(&o.A, o.vec, o.J, o.ldb_row, o.ldb_col, o.q, &o.C, o.precision, A, C, P);
         if (rc) return rc;
-        if (P.rows.nd > kBD || P.kernel == K_TTM_TC) { direct = true; return TL_OK; }
+        if (P.rows.nd > kBD || P.kernel == K_TTM_TC || ttm_simt_splits(P, sms, nullptr) > 1) {
+            direct = true;
+            return TL_OK;
+        }
         b.dtype = A.dtype;
         b.nd = P.rows.nd;
         for (int d = 0; d < P.rows.nd; ++d) {

@@ -20,8 +20,13 @@ int launch_ew_tma(const EwPlan& P, const void* A, const void* B, double alpha, v
 // TL_ETIMEOUT if a bounded wait of the TMA entrywise kernel gave up.
 int ew_status(bool clear);
 
+// k splits of the SIMT ttm (1 = none) and the k values per split; the
+// workspace of the partial sums; kernels one call launches.
+int64_t ttm_simt_splits(const TtmPlan& P, int num_sms, int64_t* kchunk);
+size_t ttm_simt_workspace_bytes(const TtmPlan& P, int num_sms);
+int ttm_simt_launches(const TtmPlan& P, int num_sms);
 int launch_ttm_simt(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate,
-                    int num_sms, cudaStream_t st);
+                    void* ws, int num_sms, cudaStream_t st);
 
 // Deterministic FP64 sum-of-squares reduction over a collapsed space with
 // operand 0 = X (dtype dx) and, when R != nullptr, operand 1 = R (dtype dr):

@@ -8,6 +8,10 @@
 // paper's "slice-times-matrix" reading of ttm (Sec. 5.2), with all slices
 // batched into one launch.  Each CTA computes a 64 x 64 (m, j) tile with a
 // 16-deep k slab staged in shared memory; each thread holds 4 x 4 outputs.
+// When the (m, j) tiles cannot fill the GPU and n_q is long (a few rows of a
+// matrix-like tensor contracted over most of its elements), the k range is
+// split across CTAs: split s writes its partial M x J block to a workspace
+// and a second kernel adds the splits in order (deterministic) into C.
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -27,6 +31,8 @@ struct TtmArgs {
     int64_t M, J, nq, saq, scq, ldb_row, ldb_col;
     int64_t tiles_m, tiles_j;
     int accumulate;
+    int64_t splits, kchunk;   // k splits; > 1: partials go to ws[s][m][j]
+    void* ws;
 };
 
 template <typename T>
@@ -43,9 +49,12 @@ __global__ void __launch_bounds__(kThreads) ttm_simt_kernel(const TtmArgs a)
     const bool a_kfast = (a.saq == 1);
     const bool b_kfast = (a.ldb_col == 1);
     const int64_t ntiles = a.tiles_m * a.tiles_j;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int64_t w = blockIdx.x; w < ntiles * a.splits; w += gridDim.x) {
+        const int64_t tile = w % ntiles, split = w / ntiles;
         const int64_t m0 = (tile % a.tiles_m) * BM;
         const int64_t j0 = (tile / a.tiles_m) * BJ;
+        const int64_t kb = split * a.kchunk;
+        const int64_t ke = min(a.nq, kb + a.kchunk);
         __syncthreads();
         if (tid < BM) {
             int64_t m = m0 + tid;
@@ -59,7 +68,7 @@ __global__ void __launch_bounds__(kThreads) ttm_simt_kernel(const TtmArgs a)
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-        for (int64_t k0 = 0; k0 < a.nq; k0 += BK) {
+        for (int64_t k0 = kb; k0 < ke; k0 += BK) {
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < (BM * BK) / kThreads; ++r) {
@@ -68,7 +77,7 @@ __global__ void __launch_bounds__(kThreads) ttm_simt_kernel(const TtmArgs a)
                 if (a_kfast) { kk = e % BK; mm = e / BK; }
                 else { mm = e % BM; kk = e / BM; }
                 int64_t m = m0 + mm, k = k0 + kk;
-                As[kk][mm] = (m < a.M && k < a.nq) ? __ldg(A + offA[mm] + k * a.saq) : T(0);
+                As[kk][mm] = (m < a.M && k < ke) ? __ldg(A + offA[mm] + k * a.saq) : T(0);
             }
 #pragma unroll
             for (int r = 0; r < (BJ * BK) / kThreads; ++r) {
@@ -77,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) ttm_simt_kernel(const TtmArgs a)
                 if (b_kfast) { kk = e % BK; jj = e / BK; }
                 else { jj = e % BJ; kk = e / BJ; }
                 int64_t j = j0 + jj, k = k0 + kk;
-                Bs[kk][jj] = (j < a.J && k < a.nq) ? __ldg(B + j * a.ldb_row + k * a.ldb_col) : T(0);
+                Bs[kk][jj] = (j < a.J && k < ke) ? __ldg(B + j * a.ldb_row + k * a.ldb_col) : T(0);
             }
             __syncthreads();
 #pragma unroll
@@ -101,16 +110,39 @@ __global__ void __launch_bounds__(kThreads) ttm_simt_kernel(const TtmArgs a)
             for (int j = 0; j < 4; ++j) {
                 int64_t jg = j0 + tj + 16 * j;
                 if (jg >= a.J) continue;
-                T* c = C + offC[tm + 16 * i] + jg * a.scq;
-                *c = a.accumulate ? *c + acc[i][j] : acc[i][j];
+                if (a.splits > 1) {
+                    static_cast<T*>(a.ws)[(split * a.M + m) * a.J + jg] = acc[i][j];
+                } else {
+                    T* c = C + offC[tm + 16 * i] + jg * a.scq;
+                    *c = a.accumulate ? *c + acc[i][j] : acc[i][j];
+                }
             }
         }
     }
 }
 
+// C(m, j) (+)= sum over splits s = 0, 1, ... of ws[s][m][j].
+template <typename T>
+__global__ void __launch_bounds__(kThreads) ttm_splitk_reduce(const TtmArgs a)
+{
+    const T* __restrict__ ws = static_cast<const T*>(a.ws);
+    T* __restrict__ C = static_cast<T*>(a.C);
+    const int64_t total = a.M * a.J;
+    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * kThreads) {
+        const int64_t m = e / a.J, j = e - m * a.J;
+        T acc = T(0);
+        for (int64_t s = 0; s < a.splits; ++s) acc += ws[s * total + e];
+        int64_t off[2];
+        map_offsets<2>(a.rows, m, 1, off);
+        T* c = C + off[1] + j * a.scq;
+        *c = a.accumulate ? *c + acc : acc;
+    }
+}
+
 template <typename T>
 int launch_typed(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate,
-                 int num_sms, cudaStream_t st)
+                 void* ws, int num_sms, cudaStream_t st)
 {
     TtmArgs a{};
     a.A = A;
@@ -127,20 +159,64 @@ int launch_typed(const TtmPlan& P, const void* A, const void* B, void* C, int ac
     a.tiles_m = (P.M + BM - 1) / BM;
     a.tiles_j = (P.J + BJ - 1) / BJ;
     a.accumulate = accumulate;
-    int64_t ntiles = a.tiles_m * a.tiles_j;
+    int64_t kchunk = 0;
+    a.splits = ttm_simt_splits(P, num_sms, &kchunk);
+    a.kchunk = a.splits > 1 ? kchunk : P.nq;
+    a.ws = ws;
+    if (a.splits > 1 && !ws) return TL_ENOMEM;
+    int64_t work = a.tiles_m * a.tiles_j * a.splits;
     int64_t cap = (int64_t)num_sms * 4;
-    int grid = (int)(ntiles < cap ? ntiles : cap);
+    int grid = (int)(work < cap ? work : cap);
     ttm_simt_kernel<T><<<grid, kThreads, 0, st>>>(a);
+    if (a.splits > 1) {
+        int64_t blocks = (P.M * P.J + kThreads - 1) / kThreads;
+        if (blocks > cap) blocks = cap;
+        ttm_splitk_reduce<T><<<(int)blocks, kThreads, 0, st>>>(a);
+    }
     return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
 }
 
 }  // namespace
 
-int launch_ttm_simt(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate,
-                    int num_sms, cudaStream_t st)
+int64_t ttm_simt_splits(const TtmPlan& P, int num_sms, int64_t* kchunk)
 {
-    if (P.dtype == TL_F64) return launch_typed<double>(P, A, B, C, accumulate, num_sms, st);
-    return launch_typed<float>(P, A, B, C, accumulate, num_sms, st);
+    // split k when the tiles cover less than half of two CTAs per SM and each
+    // split still gets at least 16 k slabs; the partials stay below 256 MB
+    const int64_t tiles = ((P.M + BM - 1) / BM) * ((P.J + BJ - 1) / BJ);
+    const int64_t target = (int64_t)num_sms * 4;
+    int64_t splits = 1;
+    if (tiles * 2 < target && P.nq >= 2 * 16 * BK) {
+        splits = (target + tiles - 1) / tiles;
+        const int64_t most = P.nq / (16 * BK);
+        if (splits > most) splits = most;
+        const int64_t elem = P.dtype == TL_F64 ? 8 : 4;
+        const int64_t per = P.M * P.J * elem;
+        while (splits > 1 && splits * per > (int64_t(256) << 20)) splits /= 2;
+    }
+    if (splits < 1) splits = 1;
+    int64_t kc = (P.nq + splits - 1) / splits;
+    kc = (kc + BK - 1) / BK * BK;
+    if (kchunk) *kchunk = kc;
+    return splits > 1 ? (P.nq + kc - 1) / kc : 1;
+}
+
+size_t ttm_simt_workspace_bytes(const TtmPlan& P, int num_sms)
+{
+    const int64_t splits = ttm_simt_splits(P, num_sms, nullptr);
+    if (splits <= 1) return 0;
+    return (size_t)splits * P.M * P.J * (P.dtype == TL_F64 ? 8 : 4);
+}
+
+int ttm_simt_launches(const TtmPlan& P, int num_sms)
+{
+    return ttm_simt_splits(P, num_sms, nullptr) > 1 ? 2 : 1;
+}
+
+int launch_ttm_simt(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate,
+                    void* ws, int num_sms, cudaStream_t st)
+{
+    if (P.dtype == TL_F64) return launch_typed<double>(P, A, B, C, accumulate, ws, num_sms, st);
+    return launch_typed<float>(P, A, B, C, accumulate, ws, num_sms, st);
 }
 
 }  // namespace tl

@@ -8,7 +8,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import TOL, get, put, rel_err, to_dev, ttm_case
+from gpu_util import TOL, TORCH, get, put, rel_err, to_dev, ttm_case
 
 pytestmark = pytest.mark.gpu
 
@@ -100,3 +100,26 @@ def test_ttm_full_scale_sampled(tl, cuda_dev, scale_tensors):
             idx = np.stack([g.integers(0, x, size=3000) for x in n], axis=1)
             ref = oracle.ttm_at(mem, n, wA, q, Bm.reshape(-1), 128, 1, idx)
             assert rel_err(got[tuple(idx.T)], ref) <= 1e-5, (pi, q)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n,q,J,pi", [((3, 200000), 2, 10, (1, 2)), ((240001, 4), 1, 34, (2, 1)),
+                                      ((5, 30011, 3), 2, 7, (3, 1, 2)), ((2, 70000), 2, 1, (1, 2))])
+def test_ttm_split_k_long_contraction(tl, cuda_dev, dtype, n, q, J, pi):
+    # few rows and a long contraction: the k range is split across CTAs and the
+    # partial sums are added in a fixed order by a second kernel
+    import json
+    X = synth.uniform(n, 4400 + J)
+    Bm = synth.uniform((J, n[q - 1]), 4401 + J)
+    A = put(X, pi, cuda_dev, dtype)
+    nout = tuple(J if r == q - 1 else x for r, x in enumerate(n))
+    C = torch.empty(int(np.prod(nout)), dtype=TORCH[dtype], device=cuda_dev)
+    rc, js = tl.tl_plan_describe(tl.TL_OP_TTM, tl.Desc(A, n, pi), None, q, J, 0, 0,
+                                 tl.Desc(C, nout, pi))
+    assert rc == 0 and json.loads(js)["splits"] > 1, js
+    got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pi, dtype)
+    assert rel_err(got, ref) <= TOL[dtype]
+    # accumulate through the split path
+    C0 = synth.uniform(nout, 4402)
+    got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pi, dtype, accumulate=True, C0=C0)
+    assert rel_err(got, ref) <= TOL[dtype]
