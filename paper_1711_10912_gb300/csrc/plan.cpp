@@ -129,6 +129,7 @@ const char* kernel_name(int k)
     case K_TTM_SIMT: return "ttm_simt";
     case K_TTM_TC: return "ttm_tc";
     case K_EW_TMA: return "ew_tma";
+    case K_TTM_ROWS: return "ttm_rows";
     default: return "none";
     }
 }
@@ -235,6 +236,12 @@ int plan_ttm(const Tensor& A, int64_t J, int64_t ldb_row, int64_t ldb_col, uint3
     P.M = P.rows.count();
     P.kernel = K_TTM_SIMT;
     P.tc_variant = 0;
+    // short contractions: a row per thread with the matrix in shared memory
+    // (at most 32 KB of it), unless the tensor-core path takes the call below
+    {
+        const int64_t Jp = (J + 15) / 16 * 16;
+        if (P.nq <= 64 && P.nq * Jp * (int64_t)A.elem() <= 32 * 1024) P.kernel = K_TTM_ROWS;
+    }
     // Tensor-core path: FP32 data in a tensor-core precision, a contraction
     // and output width worth an MMA, and an A that a TMA box can describe
     // (16-byte aligned base and strides).
@@ -331,6 +338,18 @@ int plan_entrywise(int32_t op, const Tensor& A, const Tensor* B, const Tensor& C
         if (v) {
             P.kernel = K_EW_ROWS;
             P.vec = V;
+        }
+    }
+    // Tiles over (dim 0, dim t) with both extents far below the 32-element
+    // tile edge would leave most threads idle (high-order tensors with small
+    // extents): map every element instead.
+    if (P.kernel == K_EW_TILE) {
+        auto fill = [](int64_t n) { return (double)n / (double)((n + 31) / 32 * 32); };
+        if (fill(P.sp.d[0].n) * fill(P.sp.d[P.tdim].n) < 0.2) {
+            P.kernel = K_EW_GENERIC;
+            P.vec = 1;
+            P.tdim = -1;
+            return TL_OK;
         }
     }
     // FP32 tiles and permuted rows go through TMA-staged 32 x 32 tiles when

@@ -80,6 +80,7 @@ enum Kernel : int {
     K_TTM_SIMT,       // register-tiled FP32 / FP64 batched GEMM
     K_TTM_TC,         // tcgen05 tensor-core batched GEMM
     K_EW_TMA,         // FP32, layouts differ, <= 5 dims: TMA-staged 32 x 32 tiles
+    K_TTM_ROWS,       // SIMT ttm with n_q <= 32: a row per thread, B in shared memory
 };
 
 const char* kernel_name(int k);

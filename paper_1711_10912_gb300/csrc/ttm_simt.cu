@@ -7,7 +7,8 @@
 // own A and C offsets (from the mapper) and whose k stride is w_q of A: the
 // paper's "slice-times-matrix" reading of ttm (Sec. 5.2), with all slices
 // batched into one launch.  Each CTA computes a 64 x 64 (m, j) tile with a
-// 16-deep k slab staged in shared memory; each thread holds 4 x 4 outputs.
+// 16-deep k slab staged in shared memory; each thread holds 4 x 4 outputs
+// (ttm_rows_kernel below takes short contractions).
 // When the (m, j) tiles cannot fill the GPU and n_q is long (a few rows of a
 // matrix-like tensor contracted over most of its elements), the k range is
 // split across CTAs: split s writes its partial M x J block to a workspace
@@ -121,6 +122,63 @@ __global__ void __launch_bounds__(kThreads) ttm_simt_kernel(const TtmArgs a)
     }
 }
 
+// Short contractions (n_q <= 64) with the whole matrix in shared memory: one
+// row of A per thread, 16 of its outputs accumulated in registers per pass; k
+// streams in groups of 8 loads (a further pass re-reads the row from L1/L2),
+// so every thread works and B is read as shared-memory broadcasts.  Stores run
+// along j for one row; rows are contiguous in C whenever j is not.
+constexpr int kRowsJB = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem_rows[];
+    T* Bs = reinterpret_cast<T*>(smem_rows);     // [n_q][Jp], zero beyond J
+    const T* __restrict__ A = static_cast<const T*>(a.A);
+    const T* __restrict__ B = static_cast<const T*>(a.B);
+    T* __restrict__ C = static_cast<T*>(a.C);
+    const int nq = (int)a.nq, J = (int)a.J;
+    const int Jp = (J + kRowsJB - 1) / kRowsJB * kRowsJB;
+    for (int e = threadIdx.x; e < nq * Jp; e += kThreads) {
+        const int k = e / Jp, j = e - k * Jp;
+        Bs[e] = j < J ? __ldg(B + j * a.ldb_row + k * a.ldb_col) : T(0);
+    }
+    __syncthreads();
+    for (int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x; m < a.M;
+         m += (int64_t)gridDim.x * kThreads) {
+        int64_t off[2];
+        map_offsets<2>(a.rows, m, 1, off);
+        const T* pa = A + off[0];
+        T* pc = C + off[1];
+        for (int j0 = 0; j0 < J; j0 += kRowsJB) {
+            T acc[kRowsJB];
+#pragma unroll
+            for (int j = 0; j < kRowsJB; ++j) acc[j] = T(0);
+            for (int k0 = 0; k0 < nq; k0 += 8) {
+                T x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    x[u] = k0 + u < nq ? __ldg(pa + (int64_t)(k0 + u) * a.saq) : T(0);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (k0 + u < nq) {
+                        const T* br = Bs + (k0 + u) * Jp + j0;
+#pragma unroll
+                        for (int j = 0; j < kRowsJB; ++j) acc[j] = fma(x[u], br[j], acc[j]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kRowsJB; ++j) {
+                if (j0 + j < J) {
+                    T* c = pc + (int64_t)(j0 + j) * a.scq;
+                    *c = a.accumulate ? *c + acc[j] : acc[j];
+                }
+            }
+        }
+    }
+}
+
 // C(m, j) (+)= sum over splits s = 0, 1, ... of ws[s][m][j].
 template <typename T>
 __global__ void __launch_bounds__(kThreads) ttm_splitk_reduce(const TtmArgs a)
@@ -164,8 +222,23 @@ int launch_typed(const TtmPlan& P, const void* A, const void* B, void* C, int ac
     a.kchunk = a.splits > 1 ? kchunk : P.nq;
     a.ws = ws;
     if (a.splits > 1 && !ws) return TL_ENOMEM;
-    int64_t work = a.tiles_m * a.tiles_j * a.splits;
     int64_t cap = (int64_t)num_sms * 4;
+    if (P.kernel == K_TTM_ROWS) {
+        const int Jp = (int)((P.J + kRowsJB - 1) / kRowsJB * kRowsJB);
+        const size_t smem = (size_t)P.nq * Jp * sizeof(T);
+        static bool attr[2] = {false, false};
+        if (!attr[sizeof(T) == 8]) {
+            cudaFuncSetAttribute(ttm_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 48 * 1024);
+            attr[sizeof(T) == 8] = true;
+        }
+        int64_t blocks = (P.M + kThreads - 1) / kThreads;
+        const int64_t rcap = (int64_t)num_sms * 8;
+        if (blocks > rcap) blocks = rcap;
+        ttm_rows_kernel<T><<<(int)blocks, kThreads, smem, st>>>(a);
+        return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
+    }
+    int64_t work = a.tiles_m * a.tiles_j * a.splits;
     int grid = (int)(work < cap ? work : cap);
     ttm_simt_kernel<T><<<grid, kThreads, 0, st>>>(a);
     if (a.splits > 1) {
@@ -180,6 +253,10 @@ int launch_typed(const TtmPlan& P, const void* A, const void* B, void* C, int ac
 
 int64_t ttm_simt_splits(const TtmPlan& P, int num_sms, int64_t* kchunk)
 {
+    if (P.kernel == K_TTM_ROWS) {
+        if (kchunk) *kchunk = P.nq;
+        return 1;
+    }
     // split k when the tiles cover less than half of two CTAs per SM and each
     // split still gets at least 16 k slabs; the partials stay below 256 MB
     const int64_t tiles = ((P.M + BM - 1) / BM) * ((P.J + BJ - 1) / BJ);

@@ -137,9 +137,13 @@ def test_entrywise_kernel_choice(tl):
     rc, P = _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, n6, (1, 2, 3, 4, 5, 6)),
                   _desc(tl, n6, (1, 6, 5, 4, 3, 2), addr=FAKE * 4096), eop=tl.TL_COPY)
     assert rc == 0 and P["kernel"] == "ew_rows", P
+    rc, P = _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, (63, 61, 3), (1, 2, 3)),
+                  _desc(tl, (63, 61, 3), (2, 1, 3), addr=FAKE * 4096), eop=tl.TL_COPY)
+    assert rc == 0 and P["kernel"] == "ew_tile", P
+    # tiles of small extents would be mostly empty: every element is mapped
     rc, P = _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, (5, 7, 3), (1, 2, 3)),
                   _desc(tl, (5, 7, 3), (2, 1, 3), addr=FAKE * 4096), eop=tl.TL_COPY)
-    assert rc == 0 and P["kernel"] == "ew_tile", P
+    assert rc == 0 and P["kernel"] == "ew_generic", P
 
 
 def test_validation_errors(tl):

@@ -173,3 +173,25 @@ def test_entrywise_tma_tiles_bit_exact(tl, cuda_dev, shape, op):
         got, ref = ew_case(tl, cuda_dev, OPS[op], X, Y, pa, pb, pc, "f32")
         np.testing.assert_array_equal(got, ref)
     assert "ew_tma" in seen, seen
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_entrywise_high_order_small_extents_maps_elements(tl, cuda_dev, dtype):
+    # order 7, extents 3-13 in unrelated layouts: tiles would be mostly empty,
+    # so the planner maps every element; results stay bit-exact
+    import json
+    n = (13, 3, 7, 5, 4, 6, 3)
+    g = synth.rng(3700)
+    X = synth.normal(n, 3701, dtype=np.float64)
+    Y = synth.normal(n, 3702, dtype=np.float64) + 3.0
+    for _ in range(3):
+        pa, pb, pc = (synth.random_layout(7, g) for _ in range(3))
+        A = put(X, pa, cuda_dev, dtype)
+        B = put(Y, pb, cuda_dev, dtype)
+        C = torch.empty_like(A)
+        rc, js = tl.tl_plan_describe(tl.TL_OP_ENTRYWISE, tl.Desc(A, n, pa), tl.Desc(B, n, pb), 0,
+                                     0, 0, tl.TL_ADD, tl.Desc(C, n, pc))
+        assert rc == 0 and json.loads(js)["kernel"] in ("ew_generic", "ew_rows", "ew_tma"), js
+        for op in ("add", "div"):
+            got, ref = ew_case(tl, cuda_dev, OPS[op], X, Y, pa, pb, pc, dtype)
+            np.testing.assert_array_equal(got, ref)

@@ -123,3 +123,28 @@ def test_ttm_split_k_long_contraction(tl, cuda_dev, dtype, n, q, J, pi):
     C0 = synth.uniform(nout, 4402)
     got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pi, dtype, accumulate=True, C0=C0)
     assert rel_err(got, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n,q,J,pi,pic", [((2, 3000, 7), 1, 35, (1, 2, 3), (1, 2, 3)),
+                                          ((40, 9, 50), 2, 63, (2, 3, 1), (1, 2, 3)),
+                                          ((17, 3, 11, 5), 2, 1, (4, 2, 1, 3), (2, 4, 3, 1)),
+                                          ((300, 32), 2, 50, (2, 1), (1, 2)),
+                                          ((64, 24, 9), 3, 16, (3, 1, 2), (3, 2, 1))])
+def test_ttm_rows_short_contractions(tl, cuda_dev, dtype, n, q, J, pi, pic):
+    # n_q <= 32: a row of A per thread with the matrix in shared memory, any
+    # output layout, J beyond one 16-column pass
+    import json
+    X = synth.uniform(n, 4500 + J)
+    Bm = synth.uniform((J, n[q - 1]), 4501 + J)
+    A = put(X, pi, cuda_dev, dtype)
+    nout = tuple(J if r == q - 1 else x for r, x in enumerate(n))
+    C = torch.empty(int(np.prod(nout)), dtype=TORCH[dtype], device=cuda_dev)
+    rc, js = tl.tl_plan_describe(tl.TL_OP_TTM, tl.Desc(A, n, pi), None, q, J, 0, 0,
+                                 tl.Desc(C, nout, pic))
+    assert rc == 0 and json.loads(js)["kernel"] == "ttm_rows", js
+    got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pic, dtype)
+    assert rel_err(got, ref) <= TOL[dtype]
+    C0 = synth.uniform(nout, 4502)
+    got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pic, dtype, accumulate=True, C0=C0)
+    assert rel_err(got, ref) <= TOL[dtype]
