@@ -516,6 +516,13 @@ struct Batch {
     std::vector<tl_op> direct_ops;
 };
 
+// Operations the persistent kernel does not take: a contraction this long
+// would run serially inside one work unit (the split-K kernels spread it),
+// and an operation this large amortises its own launch, so it runs on the
+// kernel tuned for its layout (TMA tiles, staged rows, tensor cores).
+constexpr int64_t kLongContraction = 4096;
+constexpr size_t kDirectBytes = size_t(16) << 20;
+
 static int fill_op(const tl_op& o, BOp& b, size_t& bytes, bool& direct)
 {
     std::memset(&b, 0, sizeof b);
@@ -528,8 +535,11 @@ static int fill_op(const tl_op& o, BOp& b, size_t& bytes, bool& direct)
         TtvPlan P;
         int rc = prepare_ttv(&o.A, o.vec, o.incb, o.q, &o.C, sms, A, C, P);
         if (rc) return rc;
-        // a split k range (few outputs, long n_q) runs on the split-K kernels
-        if (P.out.nd > kBD || P.splits > 1) { direct = true; return TL_OK; }
+        const size_t mine = (size_t)(A.count() + C.count() + P.nq) * A.elem();
+        if (P.out.nd > kBD || (P.splits > 1 && P.nq >= kLongContraction) || mine >= kDirectBytes) {
+            direct = true;
+            return TL_OK;
+        }
         b.dtype = A.dtype;
         b.nd = P.out.nd;
         for (int d = 0; d < P.out.nd; ++d) {
@@ -550,7 +560,10 @@ static int fill_op(const tl_op& o, BOp& b, size_t& bytes, bool& direct)
         TtmPlan P;
         int rc = prepare_ttm(&o.A, o.vec, o.J, o.ldb_row, o.ldb_col, o.q, &o.C, o.precision, A, C, P);
         if (rc) return rc;
-        if (P.rows.nd > kBD || P.kernel == K_TTM_TC || ttm_simt_splits(P, sms, nullptr) > 1) {
+        const size_t mine = (size_t)(A.count() + C.count() + P.J * P.nq) * A.elem();
+        if (P.rows.nd > kBD || P.kernel == K_TTM_TC ||
+            (ttm_simt_splits(P, sms, nullptr) > 1 && P.nq >= kLongContraction) ||
+            mine >= kDirectBytes) {
             direct = true;
             return TL_OK;
         }
@@ -579,7 +592,10 @@ static int fill_op(const tl_op& o, BOp& b, size_t& bytes, bool& direct)
         bool unary = o.entry_op == TL_COPY || o.entry_op == TL_SCALE;
         int rc = prepare_entrywise(o.entry_op, &o.A, unary ? nullptr : &o.B, &o.C, A, B, C, hasB, P);
         if (rc) return rc;
-        if (P.sp.nd > kBD) { direct = true; return TL_OK; }
+        if (P.sp.nd > kBD || (size_t)((hasB ? 3 : 2) * A.count()) * A.elem() >= kDirectBytes) {
+            direct = true;
+            return TL_OK;
+        }
         b.dtype = A.dtype;
         b.nd = P.sp.nd;
         for (int d = 0; d < P.sp.nd; ++d) {
