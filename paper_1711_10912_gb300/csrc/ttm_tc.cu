@@ -252,6 +252,7 @@ struct TcArgs {
     int nacc;                // TMEM accumulator buffers (2 when Jp <= 256)
     int accumulate;
     int vec_out;             // j contiguous in C, 16-byte aligned rows: float4 stores
+    int vec_rows;            // rows contiguous in C (COL), 16-byte aligned: float4 along rows
     int64_t ntiles;
     int64_t M;               // ROW: rows; COL: inner extent
     int64_t tiles_per_o;     // COL
@@ -261,10 +262,12 @@ struct TcArgs {
     uint32_t a_stage_bytes;  // FP32 staging tile
     uint32_t opa_part_bytes, opb_part_bytes;
     uint32_t off_stg, off_op, op_stage_bytes, off_bar, off_epi;
+    int b_resident;          // the whole converted B stays in shared memory at off_b
+    uint32_t off_b, b_bytes;
 };
 
 struct Bars {
-    uint32_t stg_full, stg_empty, op_full, op_empty, acc_full, acc_empty, tmem_slot;
+    uint32_t stg_full, stg_empty, op_full, op_empty, acc_full, acc_empty, b_full, tmem_slot;
 };
 
 __device__ __forceinline__ Bars bar_layout(uint32_t base, const TcArgs& a)
@@ -276,8 +279,23 @@ __device__ __forceinline__ Bars bar_layout(uint32_t base, const TcArgs& a)
     b.op_empty = b.op_full + 8 * a.ns_op;
     b.acc_full = b.op_empty + 8 * a.ns_op;
     b.acc_empty = b.acc_full + 16;
-    b.tmem_slot = b.acc_empty + 16;
+    b.b_full = b.acc_empty + 16;
+    b.tmem_slot = b.b_full + 8;
     return b;
+}
+
+// 4 x 4 transpose among the lanes 4g..4g+3: on entry lane j holds row j
+// (v = M[j][0..3]); on exit it holds column j (v = M[0..3][j]).
+__device__ __forceinline__ void transpose4(float4& v, int j)
+{
+    const bool odd = j & 1, hi = j & 2;
+    const float r0 = __shfl_xor_sync(0xffffffffu, odd ? v.x : v.y, 1);
+    const float r1 = __shfl_xor_sync(0xffffffffu, odd ? v.z : v.w, 1);
+    const float u00 = odd ? r0 : v.x, u01 = odd ? r1 : v.z;
+    const float u10 = odd ? v.y : r0, u11 = odd ? v.w : r1;
+    const float q0 = __shfl_xor_sync(0xffffffffu, hi ? u00 : u01, 2);
+    const float q1 = __shfl_xor_sync(0xffffffffu, hi ? u10 : u11, 2);
+    v = hi ? make_float4(q0, q1, u01, u11) : make_float4(u00, u10, q0, q1);
 }
 
 // Pipeline position: stage index and the parity of its current phase.
@@ -317,13 +335,14 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
             mbar_init(bars.stg_empty + 8 * s, kConvThreads);
         }
         for (int s = 0; s < a.ns_op; ++s) {
-            mbar_init(bars.op_full + 8 * s, 1 + kConvThreads);
+            mbar_init(bars.op_full + 8 * s, (a.b_resident ? 0 : 1) + kConvThreads);
             mbar_init(bars.op_empty + 8 * s, 1);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(bars.acc_full + 8 * s, 1);
             mbar_init(bars.acc_empty + 8 * s, kEpiThreads);
         }
+        mbar_init(bars.b_full, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
@@ -341,7 +360,10 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
     auto op_a = [&](int stage, int part) -> uint32_t {
         return base + a.off_op + stage * a.op_stage_bytes + part * a.opa_part_bytes;
     };
+    // streamed B: in the operand stage after A's parts; resident B: the image
+    // tile of k stage `ks` (passed as `stage`)
     auto op_b = [&](int stage, int part) -> uint32_t {
+        if (a.b_resident) return base + a.off_b + (uint32_t)(stage * kParts + part) * a.opb_part_bytes;
         return base + a.off_op + stage * a.op_stage_bytes + kParts * a.opa_part_bytes +
                part * a.opb_part_bytes;
     };
@@ -353,6 +375,14 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
             bool ok = true;
             // parity of the last arm of each stage, to drain on exit
             uint32_t stg_armed = 0, stg_par = 0, op_armed = 0, op_par = 0;
+            if (a.b_resident) {
+                // the whole converted B, once per CTA, in 64 KB pieces
+                mbar_arrive_tx(bars.b_full, a.b_bytes);
+                for (uint32_t o = 0; o < a.b_bytes; o += 65536u) {
+                    const uint32_t n = a.b_bytes - o < 65536u ? a.b_bytes - o : 65536u;
+                    bulk_load(base + a.off_b + o, a.bimg + o, n, bars.b_full);
+                }
+            }
             for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
                 int64_t o = 0, r0;
                 if (a.variant == V_COL) {
@@ -373,6 +403,7 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
                     stg_armed |= 1u << st.idx;
                     stg_par = (stg_par & ~(1u << st.idx)) | (st.phase << st.idx);
                     st.next(a.ns_stg);
+                    if (a.b_resident) continue;
 
                     if (!(ok = mbar_wait(bars.op_empty + 8 * op.idx, op.phase ^ 1u))) break;
                     uint32_t ob = bars.op_full + 8 * op.idx;
@@ -384,6 +415,13 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
                     op_armed |= 1u << op.idx;
                     op_par = (op_par & ~(1u << op.idx)) | (op.phase << op.idx);
                     op.next(a.ns_op);
+                }
+            }
+            if (!ok || a.b_resident) {
+                // the resident B must have landed before the CTA can exit
+                if (a.b_resident) {
+                    long long t0 = clock64();
+                    while (!mbar_try(bars.b_full, 0u) && clock64() - t0 < kTimeoutCycles) {}
                 }
             }
             if (!ok) {
@@ -408,6 +446,8 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
             Pipe op, acc;
             bool ok = true;
             const int nchunks = (a.Jp + 255) / 256;
+            if (a.b_resident) ok = mbar_wait(bars.b_full, 0u);
+            if (ok) tc_fence_after();
             for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
                 if (!(ok = mbar_wait(bars.acc_empty + 8 * acc.idx, acc.phase ^ 1u))) break;
                 tc_fence_after();
@@ -424,13 +464,14 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
                             const uint32_t aoff = sub * 2 * kLbo;
                             const uint32_t d = dcol + 256u * c;
                             uint32_t accum = (ks > 0 || sub > 0) ? 1u : 0u;
+                            const int bs = a.b_resident ? ks : op.idx;
                             umma<kTF32>(d, umma_desc(op_a(op.idx, 0) + aoff, kLbo, kSbo),
-                                        umma_desc(op_b(op.idx, 0) + boff, kLbo, kSbo), idesc, accum);
+                                        umma_desc(op_b(bs, 0) + boff, kLbo, kSbo), idesc, accum);
                             if constexpr (kParts == 2) {
                                 umma<kTF32>(d, umma_desc(op_a(op.idx, 0) + aoff, kLbo, kSbo),
-                                            umma_desc(op_b(op.idx, 1) + boff, kLbo, kSbo), idesc, 1u);
+                                            umma_desc(op_b(bs, 1) + boff, kLbo, kSbo), idesc, 1u);
                                 umma<kTF32>(d, umma_desc(op_a(op.idx, 1) + aoff, kLbo, kSbo),
-                                            umma_desc(op_b(op.idx, 0) + boff, kLbo, kSbo), idesc, 1u);
+                                            umma_desc(op_b(bs, 0) + boff, kLbo, kSbo), idesc, 1u);
                             }
                         }
                     }
@@ -574,6 +615,33 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
                         }
                     }
                     __syncwarp();
+                } else if (a.vec_rows) {
+                    // rows contiguous in C: a 4 x 4 transpose among lanes 4g..4g+3
+                    // turns four rows x four columns into one 16-byte vector of
+                    // four rows per lane; eight lanes write 128 contiguous bytes
+                    const int g = lane >> 2, jj = lane & 3;
+                    const int64_t r0 = rbase + 4 * g;
+                    const int64_t nr = a.M - r0;              // rows of this vector that exist
+#pragma unroll
+                    for (int c = 0; c < 32; c += 4) {
+                        float4 x = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+                        transpose4(x, jj);
+                        const int jg = c0 + c + jj;
+                        if (jg < a.J && nr > 0) {
+                            float* p = a.C + obase + r0 + (int64_t)jg * a.scq;
+                            if (nr >= 4) {
+                                float4* p4 = reinterpret_cast<float4*>(p);
+                                if (a.accumulate) {
+                                    const float4 o = *p4;
+                                    x.x += o.x; x.y += o.y; x.z += o.z; x.w += o.w;
+                                }
+                                *p4 = x;
+                            } else {
+                                const float e[4] = {x.x, x.y, x.z, x.w};
+                                for (int q = 0; q < nr; ++q) p[q] = a.accumulate ? p[q] + e[q] : e[q];
+                            }
+                        }
+                    }
                 } else if (lane < nrows) {
                     float* pc = a.C + obase + (rbase + lane) * a.sc_m;
 #pragma unroll
@@ -666,8 +734,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 }
 
 struct Layout {
-    int nparts, esize, Jp, nks, ns_stg, ns_op, nacc;
+    int nparts, esize, Jp, nks, ns_stg, ns_op, nacc, b_resident;
     uint32_t a_stage, opa_part, opb_part, op_stage, off_stg, off_op, off_epi, off_bar, smem;
+    uint32_t off_b, b_bytes;
 };
 
 Layout layout_for(const TtmPlan& P)
@@ -681,9 +750,14 @@ Layout layout_for(const TtmPlan& P)
     L.a_stage = BM * BK * 4;
     L.opa_part = BM * BK * L.esize;
     L.opb_part = (uint32_t)L.Jp * BK * L.esize;
-    L.op_stage = L.nparts * (L.opa_part + L.opb_part);
+    // a converted B of at most 64 KB stays in shared memory for the whole
+    // launch (loaded once per CTA) instead of streaming with every k stage
+    L.b_bytes = (uint32_t)L.nks * L.nparts * L.opb_part;
+    L.b_resident = L.b_bytes <= 64u * 1024u ? 1 : 0;
+    L.op_stage = L.nparts * (L.opa_part + (L.b_resident ? 0 : L.opb_part));
     const uint32_t epi = kEpiWarps * 32 * 33 * 4;        // epilogue transpose tiles
-    const uint32_t budget = 227 * 1024 - 1024 - 512 - epi;   // alignment slack + barriers
+    const uint32_t budget = 227 * 1024 - 1024 - 512 - epi -
+                            (L.b_resident ? L.b_bytes : 0);   // alignment slack + barriers
     // FP32 staging keeps the HBM bytes in flight; the operand ring only has
     // to cover the convert -> MMA hand-off
     for (L.ns_op = 3; L.ns_op >= 2; --L.ns_op) {
@@ -694,9 +768,10 @@ Layout layout_for(const TtmPlan& P)
     }
     L.off_stg = 0;
     L.off_op = L.ns_stg * L.a_stage;
-    L.off_epi = L.off_op + L.ns_op * L.op_stage;
+    L.off_b = L.off_op + L.ns_op * L.op_stage;
+    L.off_epi = L.off_b + (L.b_resident ? L.b_bytes : 0);
     L.off_bar = L.off_epi + epi;
-    L.smem = L.off_bar + 8 * (2 * L.ns_stg + 2 * L.ns_op + 4) + 16 + 1024;
+    L.smem = L.off_bar + 8 * (2 * L.ns_stg + 2 * L.ns_op + 5) + 16 + 1024;
     // more than half of the SM's shared memory keeps one CTA per SM, so no
     // two CTAs ever wait on each other for the 512 TMEM columns
     if (L.smem < 116 * 1024) L.smem = 116 * 1024;
@@ -733,6 +808,9 @@ int launch_prec(const TtmPlan& P, const void* A, const void* B, void* C, int acc
         a.vec_out = (P.scq == 1 && P.J % 4 == 0 && scm % 4 == 0 &&
                      (P.tc_variant != V_COL || P.rows.nd < 2 || P.rows.d[1].s[1] % 4 == 0) &&
                      (reinterpret_cast<uintptr_t>(C) % 16) == 0) ? 1 : 0;
+        a.vec_rows = (P.tc_variant == V_COL && scm == 1 && P.scq % 4 == 0 &&
+                      (P.rows.nd < 2 || P.rows.d[1].s[1] % 4 == 0) &&
+                      (reinterpret_cast<uintptr_t>(C) % 16) == 0) ? 1 : 0;
     }
     a.opa_part_bytes = L.opa_part;
     a.opb_part_bytes = L.opb_part;
@@ -741,6 +819,9 @@ int launch_prec(const TtmPlan& P, const void* A, const void* B, void* C, int acc
     a.op_stage_bytes = L.op_stage;
     a.off_bar = L.off_bar;
     a.off_epi = L.off_epi;
+    a.b_resident = L.b_resident;
+    a.off_b = L.off_b;
+    a.b_bytes = L.b_bytes;
 
     CUtensorMap map;
     CUresult cr;
