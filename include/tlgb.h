@@ -355,8 +355,10 @@ int tl_batch_describe(const tl_batch* batch, char* buf, size_t buflen);
 /*
  * Overrides the per-unit code of every operation of one kind in a batch
  * (for tuning experiments and tests): kind TL_OP_TTV with variant
- * TL_BV_TTV_COL (a thread per output) or TL_BV_TTV_ROW4/8/32 (4, 8 or 32
- * lanes per output), TL_OP_TTM with TL_BV_TTM_32 / TL_BV_TTM_64 (row tiles)
+ * TL_BV_TTV_COL (a thread per output), TL_BV_TTV_ROW4/8/32 (4, 8 or 32
+ * lanes per output) or TL_BV_TTV_VEC (16 bytes of outputs per thread; applied
+ * only where the outputs are contiguous in A and C, unit rounded up to whole
+ * vectors), TL_OP_TTM with TL_BV_TTM_32 / TL_BV_TTM_64 (row tiles)
  * or TL_BV_TTM_SMALL (the matrix in shared memory, a row per thread; applied
  * only to operations with n_q <= 64 and J <= 64, or J <= 32 for FP64),
  * TL_OP_ENTRYWISE with TL_BV_EW.  `unit` is the outputs (rows for ttm) per
@@ -371,6 +373,7 @@ int tl_batch_describe(const tl_batch* batch, char* buf, size_t buflen);
 #define TL_BV_TTM_64    5
 #define TL_BV_EW        6
 #define TL_BV_TTM_SMALL 7
+#define TL_BV_TTV_VEC   8
 int tl_batch_set_variant(tl_batch* batch, int32_t kind, int32_t variant, int64_t unit,
                          void* stream);
 

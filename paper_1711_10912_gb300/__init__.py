@@ -43,7 +43,7 @@ TL_OP_TTV, TL_OP_TTM, TL_OP_ENTRYWISE = range(3)
 TL_CTX_PERSISTENT, TL_CTX_GRAPH = 1, 2
 TL_BATCH_GRAPH, TL_BATCH_TUNE = 1, 2
 (TL_BV_TTV_COL, TL_BV_TTV_ROW4, TL_BV_TTV_ROW8, TL_BV_TTV_ROW32, TL_BV_TTM_32, TL_BV_TTM_64,
- TL_BV_EW, TL_BV_TTM_SMALL) = range(8)
+ TL_BV_EW, TL_BV_TTM_SMALL, TL_BV_TTV_VEC) = range(9)
 
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _u32p = ctypes.POINTER(ctypes.c_uint32)

@@ -47,6 +47,7 @@ enum : int32_t {
     BV_TTM_64 = 5,       // 64 rows
     BV_EW = 6,           // one thread per element
     BV_TTM_SMALL = 7,    // B in shared memory, a row per thread, J outputs in registers
+    BV_TTV_VEC = 8,      // 16 bytes of consecutive outputs per thread (unit stride in A and C)
 };
 
 struct BOp {
@@ -104,6 +105,67 @@ __device__ void unit_ttv_col(const BOp& op, int64_t e0, int64_t e1)
         for (; k < op.nq; ++k) acc = fma(__ldg(pa + k * op.saq), __ldg(b + k * op.incb), acc);
         T* pc = static_cast<T*>(op.C) + oc;
         *pc = op.accumulate ? *pc + acc : acc;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ bool ttv_vec_ok(const BOp& op)
+{
+    constexpr int64_t V = 16 / sizeof(T);
+    if (op.nd < 1 || op.s0[0] != 1 || op.s1[0] != 1 || op.n[0] % V || op.saq % V ||
+        op.unit % V)
+        return false;
+    for (int d = 1; d < op.nd; ++d)
+        if (op.s0[d] % V || op.s1[d] % V) return false;
+    return ((reinterpret_cast<uintptr_t>(op.A) | reinterpret_cast<uintptr_t>(op.C)) & 15) == 0;
+}
+
+// Outputs contiguous in A and C along the collapsed dim 0 (its extent and
+// every other stride multiples of the vector width, 16-byte aligned bases):
+// each thread takes 16 bytes of consecutive outputs and streams A with
+// 16-byte loads, four k at a time.
+template <typename T>
+__device__ void unit_ttv_vec(const BOp& op, int64_t e0, int64_t e1)
+{
+    constexpr int V = 16 / sizeof(T);
+    using VT = typename Vec<T, V>::type;
+    const T* A = static_cast<const T*>(op.A);
+    const T* b = static_cast<const T*>(op.B);
+    for (int64_t e = e0 + (int64_t)V * threadIdx.x; e < e1; e += (int64_t)V * kThreads) {
+        int64_t oa, oc, unused;
+        bdecode(op, e, oa, oc, unused);
+        const T* pa = A + oa;
+        T acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = T(0);
+        int64_t k = 0;
+        for (; k + 4 <= op.nq; k += 4) {
+            VT x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = __ldg(reinterpret_cast<const VT*>(pa + (k + u) * op.saq));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const T bk = __ldg(b + (k + u) * op.incb);
+                const T* xe = reinterpret_cast<const T*>(&x[u]);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = fma(xe[v], bk, acc[v]);
+            }
+        }
+        for (; k < op.nq; ++k) {
+            const VT x = __ldg(reinterpret_cast<const VT*>(pa + k * op.saq));
+            const T bk = __ldg(b + k * op.incb);
+            const T* xe = reinterpret_cast<const T*>(&x);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = fma(xe[v], bk, acc[v]);
+        }
+        T* pc = static_cast<T*>(op.C) + oc;
+        if (op.accumulate) {
+            const VT o = *reinterpret_cast<const VT*>(pc);
+            const T* oe = reinterpret_cast<const T*>(&o);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] += oe[v];
+        }
+        *reinterpret_cast<VT*>(pc) = *reinterpret_cast<const VT*>(acc);
     }
 }
 
@@ -314,6 +376,12 @@ __device__ void run_unit(const BOp& op, int64_t u, uint8_t* smem)
     case BV_TTV_ROW4: unit_ttv_row<T, 4>(op, e0, e1); break;
     case BV_TTV_ROW8: unit_ttv_row<T, 8>(op, e0, e1); break;
     case BV_TTV_ROW32: unit_ttv_row<T, 32>(op, e0, e1); break;
+    case BV_TTV_VEC:
+        // the host only assigns this unit where it applies; the check keeps a
+        // stale or foreign assignment from issuing misaligned vector loads
+        if (ttv_vec_ok<T>(op)) unit_ttv_vec<T>(op, e0, e1);
+        else unit_ttv_col<T>(op, e0, e1);
+        break;
     case BV_TTM_32:
         for (int64_t m0 = e0; m0 < e1; m0 += 32) unit_ttm<T, 32>(op, m0, smem);
         break;
@@ -321,7 +389,11 @@ __device__ void run_unit(const BOp& op, int64_t u, uint8_t* smem)
         for (int64_t m0 = e0; m0 < e1; m0 += 64) unit_ttm<T, 64>(op, m0, smem);
         break;
     case BV_TTM_SMALL:
-        if (op.J <= 4) unit_ttm_small<T, 4>(op, e0, e1, smem);
+        // the matrix must fit the static shared memory (as the host checks);
+        // anything else takes the tiled unit, one 64-row tile at a time
+        if (op.nq > 64 || op.J > (sizeof(T) == 8 ? 32 : 64)) {
+            for (int64_t m0 = e0; m0 < e1; m0 += 64) unit_ttm<T, 64>(op, m0, smem);
+        } else if (op.J <= 4) unit_ttm_small<T, 4>(op, e0, e1, smem);
         else if (op.J <= 8) unit_ttm_small<T, 8>(op, e0, e1, smem);
         else if (op.J <= 16) unit_ttm_small<T, 16>(op, e0, e1, smem);
         else unit_ttm_small<T, (sizeof(T) == 8 ? 16 : 32)>(op, e0, e1, smem);
@@ -385,6 +457,18 @@ struct Candidate {
     int64_t unit;
 };
 
+// The vectorised ttv unit needs outputs contiguous in A and C along dim 0,
+// vector-aligned addresses for every output group, and whole vectors per unit.
+bool vec_ttv_host(const BOp& op)
+{
+    if (op.kind != TL_OP_TTV || op.nd < 1) return false;
+    const int64_t V = op.dtype == TL_F64 ? 2 : 4;
+    if (op.s0[0] != 1 || op.s1[0] != 1 || op.n[0] % V || op.saq % V) return false;
+    for (int d = 1; d < op.nd; ++d)
+        if (op.s0[d] % V || op.s1[d] % V) return false;
+    return (reinterpret_cast<uintptr_t>(op.A) % 16) == 0 && (reinterpret_cast<uintptr_t>(op.C) % 16) == 0;
+}
+
 // The shared-memory ttm unit takes B whole: n_q <= 64 and J <= 64 (FP32) or
 // 32 (FP64), so B fits the kernel's static shared memory.
 bool small_ttm_host(const BOp& op)
@@ -396,8 +480,11 @@ std::string class_key(const BOp& op)
 {
     auto lg = [](int64_t x) { int b = 0; while ((int64_t(1) << b) < x) ++b; return b; };
     char buf[160];
-    std::snprintf(buf, sizeof buf, "k%d|d%d|row%d|nq%d|J%d|cnt%d", op.kind, op.dtype,
-                  op.kind == TL_OP_TTV && op.saq == 1 ? 1 : 0, lg(op.nq), lg(op.J), lg(op.count));
+    // the key records which optional units apply, so a choice cached for one
+    // operation never lands on an operation the unit does not fit
+    std::snprintf(buf, sizeof buf, "k%d|d%d|row%d|nq%d|J%d|cnt%d|v%d|s%d", op.kind, op.dtype,
+                  op.kind == TL_OP_TTV && op.saq == 1 ? 1 : 0, lg(op.nq), lg(op.J), lg(op.count),
+                  vec_ttv_host(op) ? 1 : 0, small_ttm_host(op) ? 1 : 0);
     return buf;
 }
 
@@ -410,6 +497,8 @@ std::vector<Candidate> candidates(const BOp& op)
                 for (int64_t u : {512, 4096}) c.push_back({v, u});
         }
         for (int64_t u : {1024, 4096, 16384}) c.push_back({BV_TTV_COL, u});
+        if (vec_ttv_host(op))
+            for (int64_t u : {1024, 4096, 16384}) c.push_back({BV_TTV_VEC, u});
     } else if (op.kind == TL_OP_TTM) {
         for (int64_t u : {256, 1024, 4096}) {
             c.push_back({BV_TTM_32, u});
@@ -427,6 +516,7 @@ Candidate heuristic(const BOp& op)
 {
     if (op.kind == TL_OP_TTV) {
         if (op.saq == 1 && op.nq >= 32) return {BV_TTV_ROW8, 2048};
+        if (vec_ttv_host(op)) return {BV_TTV_VEC, 4096};
         return {BV_TTV_COL, 4096};
     }
     if (op.kind == TL_OP_TTM) {
@@ -434,6 +524,24 @@ Candidate heuristic(const BOp& op)
         return op.count >= 4096 ? Candidate{BV_TTM_64, 1024} : Candidate{BV_TTM_32, 256};
     }
     return {BV_EW, 65536};
+}
+
+// A candidate from the cache (or from a representative operation) as it may
+// be applied to `op`: variants of another kind, or optional units that do not
+// fit the operation, fall back to the default choice.
+Candidate sanitize(Candidate c, const BOp& op)
+{
+    bool ok = c.unit >= 1;
+    if (op.kind == TL_OP_TTV)
+        ok = ok && (c.variant == BV_TTV_COL || c.variant == BV_TTV_ROW4 || c.variant == BV_TTV_ROW8 ||
+                    c.variant == BV_TTV_ROW32 || (c.variant == BV_TTV_VEC && vec_ttv_host(op) &&
+                                                  c.unit % 4 == 0));
+    else if (op.kind == TL_OP_TTM)
+        ok = ok && (c.variant == BV_TTM_32 || c.variant == BV_TTM_64 ||
+                    (c.variant == BV_TTM_SMALL && small_ttm_host(op)));
+    else
+        ok = ok && c.variant == BV_EW;
+    return ok ? c : heuristic(op);
 }
 
 struct TuneCache {
@@ -713,7 +821,7 @@ int batch_create(const tl_op* ops, size_t count, int32_t flags, void* stream, Ba
         if (tuned) g_tune.save();
         for (BOp& b : B->host) {
             auto it = chosen.find(tag + "|" + class_key(b));
-            Candidate c = it != chosen.end() ? it->second : heuristic(b);
+            Candidate c = it != chosen.end() ? sanitize(it->second, b) : heuristic(b);
             b.variant = c.variant;
             b.unit = c.unit;
         }
@@ -824,7 +932,8 @@ int batch_set_variant(Batch* B, int32_t kind, int32_t variant, int64_t unit, voi
     if (!B || unit < 1) return TL_EINVAL;
     const bool ok_kind =
         (kind == TL_OP_TTV && (variant == BV_TTV_COL || variant == BV_TTV_ROW4 ||
-                               variant == BV_TTV_ROW8 || variant == BV_TTV_ROW32)) ||
+                               variant == BV_TTV_ROW8 || variant == BV_TTV_ROW32 ||
+                               variant == BV_TTV_VEC)) ||
         (kind == TL_OP_TTM &&
          (variant == BV_TTM_32 || variant == BV_TTM_64 || variant == BV_TTM_SMALL)) ||
         (kind == TL_OP_ENTRYWISE && variant == BV_EW);
@@ -833,8 +942,10 @@ int batch_set_variant(Batch* B, int32_t kind, int32_t variant, int64_t unit, voi
         const int64_t bm = variant == BV_TTM_32 ? 32 : 64;
         unit = (unit + bm - 1) / bm * bm;
     }
+    if (variant == BV_TTV_VEC) unit = (unit + 3) / 4 * 4;   // whole vectors per unit
     for (BOp& b : B->host)
-        if (b.kind == kind && (variant != BV_TTM_SMALL || small_ttm_host(b))) {
+        if (b.kind == kind && (variant != BV_TTM_SMALL || small_ttm_host(b)) &&
+            (variant != BV_TTV_VEC || vec_ttv_host(b))) {
             b.variant = variant;
             b.unit = unit;
         }
@@ -860,14 +971,14 @@ int batch_set_variant(Batch* B, int32_t kind, int32_t variant, int64_t unit, voi
 int batch_describe(const Batch* B, char* buf, size_t len)
 {
     if (!B || !buf || !len) return TL_EINVAL;
-    int hist[8] = {0};
-    for (const BOp& b : B->host) hist[b.variant & 7]++;
+    int hist[16] = {0};
+    for (const BOp& b : B->host) hist[b.variant & 15]++;
     std::snprintf(buf, len,
                   "{\"ops\":%zu,\"direct\":%d,\"units\":%lld,\"grid\":%d,\"bytes\":%zu,"
                   "\"variants\":{\"ttv_col\":%d,\"ttv_row4\":%d,\"ttv_row8\":%d,\"ttv_row32\":%d,"
-                  "\"ttm32\":%d,\"ttm64\":%d,\"ew\":%d,\"ttm_small\":%d}}",
+                  "\"ttm32\":%d,\"ttm64\":%d,\"ew\":%d,\"ttm_small\":%d,\"ttv_vec\":%d}}",
                   B->host.size(), B->direct, (long long)B->total_units, grid_size(), B->bytes,
-                  hist[0], hist[1], hist[2], hist[3], hist[4], hist[5], hist[6], hist[7]);
+                  hist[0], hist[1], hist[2], hist[3], hist[4], hist[5], hist[6], hist[7], hist[8]);
     return TL_OK;
 }
 
@@ -931,7 +1042,7 @@ int slot_launch(Slot* s, const tl_op* const* ops, size_t n, cudaStream_t st)
             std::lock_guard<std::mutex> lk(g_tune.mu);
             if (g_tune.loaded) {
                 auto it = g_tune.table.find(device_tag() + "|" + class_key(b));
-                if (it != g_tune.table.end()) c = it->second;
+                if (it != g_tune.table.end()) c = sanitize(it->second, b);
             }
         }
         b.variant = c.variant;

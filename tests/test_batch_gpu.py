@@ -113,7 +113,8 @@ def test_batch_matches_oracle_default_plan(tl, cuda_dev, dtype):
 
 
 @pytest.mark.parametrize("variant,unit", [("TTV_COL", 7), ("TTV_COL", 1000), ("TTV_ROW4", 5),
-                                          ("TTV_ROW8", 300), ("TTV_ROW32", 64)])
+                                          ("TTV_ROW8", 300), ("TTV_ROW32", 64), ("TTV_VEC", 6),
+                                          ("TTV_VEC", 4096)])
 def test_batch_every_ttv_variant(tl, cuda_dev, variant, unit):
     s = OpSet(tl, cuda_dev, 120, 7100, "f32")
     rc, b = tl.tl_batch_create(s.ops, 0)
@@ -225,3 +226,47 @@ def test_bounded_wait_reports_timeout_and_context_survives(tl, cuda_dev):
         s.check()
     finally:
         tl.tl_batch_destroy(b)
+
+
+_POISON_CHILD = r"""
+import json, os, sys
+sys.path[:0] = [{tests!r}, {root!r}]
+import torch
+import paper_1711_10912_gb300 as tl
+tl.load_library()
+from test_batch_gpu import OpSet
+dev = torch.device("cuda", 0)
+s = OpSet(tl, dev, 160, 7700, "f32")
+rc, b = tl.tl_batch_create(s.ops, tl.TL_BATCH_TUNE)
+tl.check(rc)
+tl.check(tl.tl_batch_run(b))
+worst = s.check()
+tl.tl_batch_destroy(b)
+print(json.dumps({{"worst": worst}}))
+"""
+
+
+def test_batch_poisoned_tune_cache_is_ignored(tl, cuda_dev, tmp_path):
+    # a cache whose entries name units that do not fit (vectorised ttv and
+    # shared-memory ttm everywhere, ragged unit sizes) must not change results:
+    # each choice is checked against the operation it is applied to
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, TL_TUNE_CACHE=str(cache))
+    code = _POISON_CHILD.format(tests=here, root=os.path.dirname(here))
+    first = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=600)
+    assert first.returncode == 0, first.stderr[-2000:]
+    lines = [ln.split() for ln in cache.read_text().splitlines() if ln.strip()]
+    assert lines
+    poisoned = []
+    for key, variant, unit in lines:
+        v = tl.TL_BV_TTV_VEC if "|k0|" in key else (tl.TL_BV_TTM_SMALL if "|k1|" in key else variant)
+        poisoned.append(f"{key} {v} 6")
+    cache.write_text("\n".join(poisoned) + "\n")
+    second = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                            timeout=600)
+    assert second.returncode == 0, second.stderr[-2000:]
+    assert json.loads(second.stdout.strip().splitlines()[-1])["worst"] <= TOL["f32"]
