@@ -235,6 +235,7 @@ const char* tl_strerror(int code)
 int tl_ttv(const tl_tensor* A_, const void* b, int64_t incb, uint32_t q, const tl_tensor* C_,
            int32_t accumulate, void* stream)
 {
+    NvtxRange nvtx_range("tl_ttv");
     Tensor A, C;
     TtvPlan P;
     int sms = device_sms();
@@ -256,6 +257,7 @@ int tl_ttv(const tl_tensor* A_, const void* b, int64_t incb, uint32_t q, const t
 int tl_ttm(const tl_tensor* A_, const void* B, int64_t J, int64_t ldb_row, int64_t ldb_col,
            uint32_t q, const tl_tensor* C_, int32_t precision, int32_t accumulate, void* stream)
 {
+    NvtxRange nvtx_range("tl_ttm");
     Tensor A, C;
     TtmPlan P;
     int sms = device_sms();
@@ -270,6 +272,7 @@ int tl_ttm(const tl_tensor* A_, const void* B, int64_t J, int64_t ldb_row, int64
 int tl_entrywise(int32_t op, const tl_tensor* A_, const tl_tensor* B_, double alpha,
                  const tl_tensor* C_, void* stream)
 {
+    NvtxRange nvtx_range("tl_entrywise");
     Tensor A, B, C;
     EwPlan P;
     bool hasB = false;
@@ -306,6 +309,7 @@ static int norm_common(const Tensor& X, const Tensor* R, double* result, cudaStr
 
 int tl_norm(const tl_tensor* A_, double* result, void* stream)
 {
+    NvtxRange nvtx_range("tl_norm");
     Tensor A;
     int rc = load_tensor(A_, false, A);
     if (rc) return rc;
@@ -315,6 +319,7 @@ int tl_norm(const tl_tensor* A_, double* result, void* stream)
 
 int tl_rel_error(const tl_tensor* X_, const tl_tensor* R_, double* result, void* stream)
 {
+    NvtxRange nvtx_range("tl_rel_error");
     Tensor X, R;
     int rc = load_tensor(X_, false, X);
     if (rc) return rc;

@@ -1082,7 +1082,11 @@ int tl_batch_create(const tl_op* ops, size_t count, int32_t flags, void* stream,
     return batch_create(ops, count, flags, stream, reinterpret_cast<Batch**>(out));
 }
 
-int tl_batch_run(tl_batch* b, void* stream) { return batch_run(reinterpret_cast<Batch*>(b), stream); }
+int tl_batch_run(tl_batch* b, void* stream)
+{
+    NvtxRange nvtx_range("tl_batch_run");
+    return batch_run(reinterpret_cast<Batch*>(b), stream);
+}
 
 int tl_batch_destroy(tl_batch* b) { return batch_destroy(reinterpret_cast<Batch*>(b)); }
 

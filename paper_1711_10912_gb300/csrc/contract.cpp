@@ -135,6 +135,7 @@ extern "C" {
 
 int tl_transpose(const tl_tensor* A_, const uint32_t* tau, const tl_tensor* C_, void* stream)
 {
+    NvtxRange nvtx_range("tl_transpose");
     Tensor A;
     int rc = load_tensor(A_, false, A);
     if (rc) return rc;
@@ -161,6 +162,7 @@ int tl_transpose(const tl_tensor* A_, const uint32_t* tau, const tl_tensor* C_, 
 int tl_ttt(const tl_tensor* A_, const uint32_t* phi, const tl_tensor* B_, const uint32_t* psi,
            uint32_t q, const tl_tensor* C_, int32_t precision, int32_t accumulate, void* stream)
 {
+    NvtxRange nvtx_range("tl_ttt");
     Tensor A, B;
     int rc = load_tensor(A_, false, A);
     if (rc) return rc;

@@ -4,10 +4,33 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
+
+#include <cstdlib>
 
 #include "plan.h"
 
 namespace tl {
+
+// An NVTX range named after an entry point, pushed when the environment
+// variable TL_NVTX is set (read once per process), so profilers can attribute
+// kernels to the ABI calls that launched them.
+struct NvtxRange {
+    bool on;
+    explicit NvtxRange(const char* name) : on(enabled())
+    {
+        if (on) nvtxRangePushA(name);
+    }
+    ~NvtxRange()
+    {
+        if (on) nvtxRangePop();
+    }
+    static bool enabled()
+    {
+        static const bool e = std::getenv("TL_NVTX") != nullptr;
+        return e;
+    }
+};
 
 int device_sms();
 // Adds n to the process-wide launch counter reported by tl_launch_count().

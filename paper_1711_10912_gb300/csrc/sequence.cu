@@ -96,6 +96,7 @@ extern "C" {
 int tl_ttvs(const tl_tensor* A_, const void* const* vecs, const uint32_t* modes, uint32_t count,
             const tl_tensor* C_, void* stream)
 {
+    NvtxRange nvtx_range("tl_ttvs");
     Tensor A, C;
     int rc = load_tensor(A_, false, A);
     if (rc) return rc;
@@ -171,6 +172,7 @@ int tl_ttvs(const tl_tensor* A_, const void* const* vecs, const uint32_t* modes,
 int tl_ttms(const tl_tensor* A_, const void* const* mats, const int64_t* J, const uint32_t* modes,
             uint32_t count, const tl_tensor* C_, int32_t precision, void* stream)
 {
+    NvtxRange nvtx_range("tl_ttms");
     Tensor A, C;
     int rc = load_tensor(A_, false, A);
     if (rc) return rc;
@@ -236,6 +238,7 @@ int tl_ttms(const tl_tensor* A_, const void* const* mats, const int64_t* J, cons
 
 int tl_hopm(const tl_tensor* A_, void* const* u, double* lambda, uint32_t K, void* stream)
 {
+    NvtxRange nvtx_range("tl_hopm");
     Tensor A;
     int rc = load_tensor(A_, false, A);
     if (rc) return rc;

@@ -175,6 +175,7 @@ void run_worker(tl_ctx* c)
                     for (auto& o : r->ops) batch_ops.push_back(&o->op);
                 // 3. launch without holding the lock
                 lk.unlock();
+                NvtxRange nvtx_range("tl_ctx_batch_launch");
                 int rc;
                 if (c->flags & TL_CTX_PERSISTENT) {
                     rc = slot_launch(free_slot->table, batch_ops.data(), batch_ops.size(),

@@ -182,3 +182,28 @@ def test_ttv_staged_row_kernel_selected_and_exact_on_integers(tl, cuda_dev):
         got, ref = ttv_case(tl, cuda_dev, X, 1, b, (1, 2), (1,), dtype)
         np.testing.assert_array_equal(got, ref)
     assert tl.tl_device_status() == tl.TL_OK
+
+
+def test_nvtx_ranges_do_not_change_results(tl, cuda_dev):
+    # TL_NVTX=1 wraps every entry point in an NVTX range (read once per
+    # process), so the check runs in a child process
+    import os
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    code = (
+        "import sys; sys.path[:0] = [%r, %r]\n"
+        "import numpy as np, torch, oracle, synth\n"
+        "import paper_1711_10912_gb300 as tl\n"
+        "tl.load_library()\n"
+        "from gpu_util import ttv_case, ttm_case, rel_err\n"
+        "dev = torch.device('cuda', 0)\n"
+        "X = synth.uniform((33, 17, 9), 4600)\n"
+        "got, ref = ttv_case(tl, dev, X, 2, synth.uniform((17,), 4601), (1, 2, 3), (2, 1), 'f64')\n"
+        "assert rel_err(got, ref) <= 1e-12\n"
+        "got, ref = ttm_case(tl, dev, X, 3, synth.uniform((5, 9), 4602), (3, 1, 2), (1, 2, 3), 'f64')\n"
+        "assert rel_err(got, ref) <= 1e-12\n"
+        "print('ok')\n" % (here, os.path.dirname(here)))
+    res = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, TL_NVTX="1"),
+                         capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0 and res.stdout.strip().endswith("ok"), res.stderr[-2000:]
