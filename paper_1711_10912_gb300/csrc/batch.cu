@@ -62,12 +62,31 @@ struct BOp {
     const void* A;
     const void* B;       // b (ttv), B (ttm), second operand (entrywise)
     void* C;
+    int32_t idx32;       // every linear index fits 32 bits: decode with fd[]
+    FastDiv fd[kBD];     // multiply-high division by n[d]
 };
 
 __device__ __forceinline__ void bdecode(const BOp& op, int64_t g, int64_t& o0, int64_t& o1,
                                         int64_t& o2)
 {
     o0 = o1 = o2 = 0;
+    if (op.idx32) {
+        uint32_t r = (uint32_t)g;
+        for (int d = 0; d < op.nd; ++d) {
+            uint32_t i = r;
+            if (d < op.nd - 1) {
+                const FastDiv f = op.fd[d];
+                const uint32_t t = __umulhi(f.mul, r);
+                const uint32_t qd = (t + ((r - t) >> f.sh1)) >> f.sh2;
+                i = r - qd * (uint32_t)op.n[d];
+                r = qd;
+            }
+            o0 += (int64_t)i * op.s0[d];
+            o1 += (int64_t)i * op.s1[d];
+            o2 += (int64_t)i * op.s2[d];
+        }
+        return;
+    }
     for (int d = 0; d < op.nd; ++d) {
         int64_t i;
         if (d == op.nd - 1) {
@@ -722,6 +741,9 @@ static int fill_op(const tl_op& o, BOp& b, size_t& bytes, bool& direct)
     } else {
         return TL_EINVAL;
     }
+    // linear indices below 2^32: 32-bit multiply-high decoding
+    b.idx32 = b.count <= (int64_t)0xffffffffLL ? 1 : 0;
+    for (int d = 0; d < b.nd; ++d) b.fd[d] = make_fastdiv((uint32_t)(b.n[d] > 0 ? b.n[d] : 1));
     return TL_OK;
 }
 

@@ -125,6 +125,33 @@ int plan_ttm(const Tensor& A, int64_t J, int64_t ldb_row, int64_t ldb_col, uint3
              const Tensor& C, int32_t precision, TtmPlan& P);
 int plan_entrywise(int32_t op, const Tensor& A, const Tensor* B, const Tensor& C, EwPlan& P);
 
+// Division of 32-bit unsigned indices by an invariant divisor d >= 1 with a
+// multiply-high, an add and two shifts (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994, Fig. 4.1): with
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, sh1 = min(l, 1),
+// sh2 = max(l - 1, 0):  n / d = (t + ((n - t) >> sh1)) >> sh2, t = mulhi(m, n).
+struct FastDiv {
+    uint32_t mul;
+    uint32_t sh1, sh2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    uint32_t l = 0;
+    while (l < 32 && (uint64_t(1) << l) < d) ++l;
+    FastDiv f;
+    f.mul = (uint32_t)(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+    f.sh1 = l < 1 ? l : 1;
+    f.sh2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+
+inline uint32_t fastdiv_host(uint32_t n, const FastDiv& f)
+{
+    const uint32_t t = (uint32_t)(((uint64_t)f.mul * n) >> 32);
+    return (t + ((n - t) >> f.sh1)) >> f.sh2;
+}
+
 // Pointer alignment helper.
 inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 

@@ -118,9 +118,31 @@ void fail(const char* what, int it)
 
 }  // namespace
 
+// The multiply-high division against plain division: small divisors, powers
+// of two and random 32-bit divisors and dividends, including the extremes.
+void check_fastdiv()
+{
+    std::vector<uint32_t> ds = {1, 2, 3, 5, 7, 10, 31, 32, 33, 63, 64, 65, 100, 127, 128, 1000,
+                                65535, 65536, 65537, 0x7fffffffu, 0x80000000u, 0xffffffffu};
+    for (int i = 0; i < 2000; ++i) ds.push_back((uint32_t)uni(1, 0xffffffffLL));
+    for (uint32_t d : ds) {
+        const FastDiv f = make_fastdiv(d);
+        std::vector<uint32_t> ns = {0, 1, d - 1, d, d + 1, 0x7fffffffu, 0x80000000u, 0xfffffffeu,
+                                    0xffffffffu};
+        for (int i = 0; i < 200; ++i) ns.push_back((uint32_t)uni(0, 0xffffffffLL));
+        for (uint32_t n : ns)
+            if (fastdiv_host(n, f) != n / d) {
+                std::fprintf(stderr, "fastdiv mismatch: %u / %u\n", n, d);
+                ++failures;
+                return;
+            }
+    }
+}
+
 int main(int argc, char** argv)
 {
     const int iters = argc > 1 ? std::atoi(argv[1]) : 2000;
+    check_fastdiv();
     static float dummy[1];
     for (int it = 0; it < iters && failures < 5; ++it) {
         const uint32_t p = (uint32_t)uni(1, 7);
