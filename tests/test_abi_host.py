@@ -163,6 +163,14 @@ def test_validation_errors(tl):
     assert _plan(tl, tl.TL_OP_TTV, A, _desc(tl, (4, 6), w=(1, 2), addr=FAKE * 4096),
                  q=2)[0] == tl.TL_EINVAL                                # self-overlapping C
     assert _plan(tl, tl.TL_OP_TTV, _desc(tl, n, w=(1, 0, 3)), C, q=2)[0] == tl.TL_EINVAL
+    # empty tensors (an extent of 0) and orders beyond the maximum are rejected
+    assert _plan(tl, tl.TL_OP_TTV, _desc(tl, (4, 0, 6)), C, q=2)[0] == tl.TL_EINVAL
+    n17 = (1,) * 17
+    assert _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, n17), _desc(tl, n17, addr=FAKE * 4096),
+                 eop=tl.TL_COPY)[0] == tl.TL_EINVAL
+    n16 = (1,) * 16
+    assert _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, n16), _desc(tl, n16, addr=FAKE * 4096),
+                 eop=tl.TL_COPY)[0] == 0
     # ttm
     Cm = _desc(tl, (4, 3, 6), addr=FAKE * 4096)
     assert _plan(tl, tl.TL_OP_TTM, A, Cm, q=2, J=3)[0] == 0
