@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-next", action="store_true",
                     help="skip the sequences / transpose / ttt / view measurements")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the small FP64 64^3 latency measurements")
     ap.add_argument("--batch-ops", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--serve-rates", default="2000,10000,40000")
@@ -507,6 +509,9 @@ def main():
         if not args.no_next:
             extras["next"] = measure_next(tl, torch, dev, sh, edge, peaks)
             torch.cuda.empty_cache()
+        if not args.no_small:
+            extras["small"] = measure_small(tl, torch, dev, sh, rank == 0)
+            torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -916,6 +921,88 @@ def measure_next(tl, torch, dev, sh, edge, peaks):
     out["ttt_bf16x3"] = {"A": list(nA), "B": list(nB), "C": list(nC),
                          "note": "frac_tensor_x3 = 3 MMAs per product / measured BF16 peak",
                          "runs": tt}
+    return out
+
+
+def measure_small(tl, torch, dev, sh, with_oracle, reps=200):
+    """The small plain-method case: order-3 FP64 64^3 (first-order), ttv along
+    mode 2, ttm along mode 1 with a 32 x 64 matrix, add with a last-order copy.
+    Everything is L2-resident, so the numbers are latencies: device time per
+    call (a CUDA graph of `reps` calls replayed, so host overhead is excluded),
+    host time per call through the Python binding (enqueue only, and enqueue +
+    synchronise), kernels launched per call, and the FP64 oracle's time per
+    call on one host core."""
+    import oracle
+    import synth
+    case = synth.small_case()
+    n = case.n
+    piF, piL = synth.first_order(3), synth.last_order(3)
+    memF, memL = synth.to_memory(case.X, piF), synth.to_memory(case.X, piL)
+    A, AL = torch.from_numpy(memF).to(dev), torch.from_numpy(memL).to(dev)
+    b = torch.from_numpy(case.b).to(dev)
+    B = torch.from_numpy(np.ascontiguousarray(case.B).reshape(-1)).to(dev)
+    J = case.B.shape[0]
+    Cv = torch.empty(n[0] * n[2], dtype=torch.float64, device=dev)
+    Cm = torch.empty(J * n[1] * n[2], dtype=torch.float64, device=dev)
+    Ce = torch.empty_like(A)
+    DA, DL = tl.Desc(A, n, piF), tl.Desc(AL, n, piL)
+    DCv, DCm, DCe = tl.Desc(Cv, (n[0], n[2])), tl.Desc(Cm, (J, n[1], n[2])), tl.Desc(Ce, n)
+    N = n[0] * n[1] * n[2]
+    calls = {
+        "ttv_q2": (lambda st: tl.tl_ttv(DA, b, 1, 2, DCv, 0, st), (N + n[0] * n[2] + n[1]) * 8),
+        "ttm_q1_32x64": (lambda st: tl.tl_ttm(DA, B, J, n[0], 1, 1, DCm, 0, 0, st),
+                         (N + J * n[1] * n[2] + J * n[0]) * 8),
+        "add_first+last": (lambda st: tl.tl_entrywise(tl.TL_ADD, DA, DL, 1.0, DCe, st), 3 * N * 8),
+    }
+    w = oracle.strides(n, piF)
+    oracle_calls = {
+        "ttv_q2": lambda: oracle.ttv(memF, n, w, 2, case.b),
+        "ttm_q1_32x64": lambda: oracle.ttm(memF, n, w, 1, case.B.reshape(-1), J, n[0], 1),
+        "add_first+last": lambda: oracle.entrywise(oracle.OP_ADD, n, memF, w, memL,
+                                                   oracle.strides(n, piL)),
+    }
+    out = {"shape": list(n), "dtype": "f64", "reps": reps, "calls": {}}
+    cap = torch.cuda.Stream(device=dev)
+    for name, (fn, byts) in calls.items():
+        # warm up on both streams (plans, per-stream workspaces)
+        for st in (sh, cap.cuda_stream):
+            for _ in range(3):
+                tl.check(fn(st))
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        l0 = tl.tl_launch_count()
+        with torch.cuda.graph(graph, stream=cap):
+            for _ in range(reps):
+                tl.check(fn(cap.cuda_stream))
+        launches = (tl.tl_launch_count() - l0) / reps
+        graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        dev_us = e0.elapsed_time(e1) * 1e3 / reps
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn(sh)
+        t_enq = (time.perf_counter() - t0) / reps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(20):
+            fn(sh)
+            torch.cuda.synchronize()
+        sync_us = (time.perf_counter() - t0) / 20 * 1e6
+        rec = {"device_us_per_call": round(dev_us, 2),
+               "host_enqueue_us_per_call": round(t_enq * 1e6, 2),
+               "host_us_per_call_synchronous": round(sync_us, 2),
+               "kernels_per_call": launches, "GB/s_device": round(byts / (dev_us / 1e6) / 1e9, 1)}
+        if with_oracle:
+            t0 = time.perf_counter()
+            for _ in range(3):
+                oracle_calls[name]()
+            rec["oracle_us_per_call_1_core"] = round((time.perf_counter() - t0) / 3 * 1e6, 1)
+        out["calls"][name] = rec
     return out
 
 

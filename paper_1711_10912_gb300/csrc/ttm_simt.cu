@@ -122,14 +122,13 @@ __global__ void __launch_bounds__(kThreads) ttm_simt_kernel(const TtmArgs a)
     }
 }
 
-// Short contractions (n_q <= 64) with the whole matrix in shared memory: one
-// row of A per thread, 16 of its outputs accumulated in registers per pass; k
-// streams in groups of 8 loads (a further pass re-reads the row from L1/L2),
-// so every thread works and B is read as shared-memory broadcasts.  Stores run
-// along j for one row; rows are contiguous in C whenever j is not.
-constexpr int kRowsJB = 16;
-
-template <typename T>
+// Short contractions (n_q <= 64) with the whole matrix in shared memory: each
+// work item is one row of A and a group of JB columns (JB = 16 when the rows
+// alone fill the GPU, down to 1 for few rows, so small problems still use
+// every SM); its outputs are accumulated in registers, k streams in groups of
+// 8 loads, B is read as shared-memory broadcasts.  Rows are contiguous in C
+// whenever j is not.
+template <typename T, int JB>
 __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem_rows[];
@@ -138,42 +137,44 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmArgs a)
     const T* __restrict__ B = static_cast<const T*>(a.B);
     T* __restrict__ C = static_cast<T*>(a.C);
     const int nq = (int)a.nq, J = (int)a.J;
-    const int Jp = (J + kRowsJB - 1) / kRowsJB * kRowsJB;
+    const int Jp = (J + JB - 1) / JB * JB;
+    const int groups = Jp / JB;
     for (int e = threadIdx.x; e < nq * Jp; e += kThreads) {
         const int k = e / Jp, j = e - k * Jp;
         Bs[e] = j < J ? __ldg(B + j * a.ldb_row + k * a.ldb_col) : T(0);
     }
     __syncthreads();
-    for (int64_t m = (int64_t)blockIdx.x * kThreads + threadIdx.x; m < a.M;
-         m += (int64_t)gridDim.x * kThreads) {
+    const int64_t items = a.M * groups;
+    for (int64_t it = (int64_t)blockIdx.x * kThreads + threadIdx.x; it < items;
+         it += (int64_t)gridDim.x * kThreads) {
+        const int64_t m = it / groups;
+        const int j0 = (int)(it - m * groups) * JB;
         int64_t off[2];
         map_offsets<2>(a.rows, m, 1, off);
         const T* pa = A + off[0];
         T* pc = C + off[1];
-        for (int j0 = 0; j0 < J; j0 += kRowsJB) {
-            T acc[kRowsJB];
+        T acc[JB];
 #pragma unroll
-            for (int j = 0; j < kRowsJB; ++j) acc[j] = T(0);
-            for (int k0 = 0; k0 < nq; k0 += 8) {
-                T x[8];
+        for (int j = 0; j < JB; ++j) acc[j] = T(0);
+        for (int k0 = 0; k0 < nq; k0 += 8) {
+            T x[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    x[u] = k0 + u < nq ? __ldg(pa + (int64_t)(k0 + u) * a.saq) : T(0);
+            for (int u = 0; u < 8; ++u)
+                x[u] = k0 + u < nq ? __ldg(pa + (int64_t)(k0 + u) * a.saq) : T(0);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (k0 + u < nq) {
-                        const T* br = Bs + (k0 + u) * Jp + j0;
+            for (int u = 0; u < 8; ++u) {
+                if (k0 + u < nq) {
+                    const T* br = Bs + (k0 + u) * Jp + j0;
 #pragma unroll
-                        for (int j = 0; j < kRowsJB; ++j) acc[j] = fma(x[u], br[j], acc[j]);
-                    }
+                    for (int j = 0; j < JB; ++j) acc[j] = fma(x[u], br[j], acc[j]);
                 }
             }
+        }
 #pragma unroll
-            for (int j = 0; j < kRowsJB; ++j) {
-                if (j0 + j < J) {
-                    T* c = pc + (int64_t)(j0 + j) * a.scq;
-                    *c = a.accumulate ? *c + acc[j] : acc[j];
-                }
+        for (int j = 0; j < JB; ++j) {
+            if (j0 + j < J) {
+                T* c = pc + (int64_t)(j0 + j) * a.scq;
+                *c = a.accumulate ? *c + acc[j] : acc[j];
             }
         }
     }
@@ -224,18 +225,23 @@ int launch_typed(const TtmPlan& P, const void* A, const void* B, void* C, int ac
     if (a.splits > 1 && !ws) return TL_ENOMEM;
     int64_t cap = (int64_t)num_sms * 4;
     if (P.kernel == K_TTM_ROWS) {
-        const int Jp = (int)((P.J + kRowsJB - 1) / kRowsJB * kRowsJB);
+        // columns per work item: as many as keep at least two CTAs per SM busy
+        const int64_t want = (int64_t)num_sms * 2 * kThreads;
+        int jb = 16;
+        while (jb > 1 && P.M * ((P.J + jb - 1) / jb) < want) jb /= 2;
+        const int Jp = (int)((P.J + jb - 1) / jb * jb);
         const size_t smem = (size_t)P.nq * Jp * sizeof(T);
-        static bool attr[2] = {false, false};
-        if (!attr[sizeof(T) == 8]) {
-            cudaFuncSetAttribute(ttm_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 48 * 1024);
-            attr[sizeof(T) == 8] = true;
-        }
-        int64_t blocks = (P.M + kThreads - 1) / kThreads;
+        const int64_t items = P.M * (Jp / jb);
+        int64_t blocks = (items + kThreads - 1) / kThreads;
         const int64_t rcap = (int64_t)num_sms * 8;
         if (blocks > rcap) blocks = rcap;
-        ttm_rows_kernel<T><<<(int)blocks, kThreads, smem, st>>>(a);
+        switch (jb) {
+        case 16: ttm_rows_kernel<T, 16><<<(int)blocks, kThreads, smem, st>>>(a); break;
+        case 8: ttm_rows_kernel<T, 8><<<(int)blocks, kThreads, smem, st>>>(a); break;
+        case 4: ttm_rows_kernel<T, 4><<<(int)blocks, kThreads, smem, st>>>(a); break;
+        case 2: ttm_rows_kernel<T, 2><<<(int)blocks, kThreads, smem, st>>>(a); break;
+        default: ttm_rows_kernel<T, 1><<<(int)blocks, kThreads, smem, st>>>(a); break;
+        }
         return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
     }
     int64_t work = a.tiles_m * a.tiles_j * a.splits;
