@@ -160,6 +160,29 @@ __device__ __forceinline__ void fence_proxy_async()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// TMA stores of a shared-memory box into C (bulk-group completion, issued and
+// waited on by one thread)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int y, int z,
+                                             uint32_t src)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the source of every committed store has been read (its shared memory may be reused)
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed store has completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -253,6 +276,7 @@ struct TcArgs {
     int accumulate;
     int vec_out;             // j contiguous in C, 16-byte aligned rows: float4 stores
     int vec_rows;            // rows contiguous in C (COL), 16-byte aligned: float4 along rows
+    int tma_out;             // C written by TMA stores of 32 x 32 boxes (no accumulation)
     int64_t ntiles;
     int64_t M;               // ROW: rows; COL: inner extent
     int64_t tiles_per_o;     // COL
@@ -284,20 +308,6 @@ __device__ __forceinline__ Bars bar_layout(uint32_t base, const TcArgs& a)
     return b;
 }
 
-// 4 x 4 transpose among the lanes 4g..4g+3: on entry lane j holds row j
-// (v = M[j][0..3]); on exit it holds column j (v = M[0..3][j]).
-__device__ __forceinline__ void transpose4(float4& v, int j)
-{
-    const bool odd = j & 1, hi = j & 2;
-    const float r0 = __shfl_xor_sync(0xffffffffu, odd ? v.x : v.y, 1);
-    const float r1 = __shfl_xor_sync(0xffffffffu, odd ? v.z : v.w, 1);
-    const float u00 = odd ? r0 : v.x, u01 = odd ? r1 : v.z;
-    const float u10 = odd ? v.y : r0, u11 = odd ? v.w : r1;
-    const float q0 = __shfl_xor_sync(0xffffffffu, hi ? u00 : u01, 2);
-    const float q1 = __shfl_xor_sync(0xffffffffu, hi ? u10 : u11, 2);
-    v = hi ? make_float4(q0, q1, u01, u11) : make_float4(u00, u10, q0, q1);
-}
-
 // Pipeline position: stage index and the parity of its current phase.
 struct Pipe {
     int idx = 0;
@@ -312,7 +322,8 @@ struct Pipe {
 
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
-ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
+ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap cmap,
+              const TcArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // align the dynamic shared memory base to 1024 bytes (128-byte swizzle atoms)
@@ -557,6 +568,9 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
         const int chalf = (warp - kEpiWarp0) >> 2;   // this warp's 32-column chunks
         // per-warp 32 x 33 staging tile: rows are TMEM lanes, columns j
         float* tile = reinterpret_cast<float*>(sbase + a.off_epi) + (warp - kEpiWarp0) * 32 * 33;
+        // TMA-store path: per-warp 32 x 32 box image (4 KB, 1024-byte aligned)
+        float* const box = reinterpret_cast<float*>(sbase + a.off_epi) + (warp - kEpiWarp0) * 32 * 32;
+        const uint32_t box_addr = base + a.off_epi + (uint32_t)(warp - kEpiWarp0) * 4096u;
         // j contiguous in C (and not i): transpose so that lanes run along j
         const bool j_fast = (a.scq == 1);
         Pipe acc;
@@ -564,9 +578,9 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
         for (int64_t tile_id = blockIdx.x; tile_id < a.ntiles && ok; tile_id += gridDim.x) {
             if (!(ok = mbar_wait(bars.acc_full + 8 * acc.idx, acc.phase))) break;
             tc_fence_after();
-            int64_t rbase, obase = 0, nrows;
+            int64_t rbase, obase = 0, nrows, o = 0;
             if (a.variant == V_COL) {
-                int64_t o = tile_id / a.tiles_per_o;
+                o = tile_id / a.tiles_per_o;
                 rbase = (tile_id % a.tiles_per_o) * BM + quarter * 32;
                 obase = o * a.sc_o;
             } else {
@@ -577,7 +591,34 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
             for (int c0 = 32 * chalf; c0 < a.Jp; c0 += 64) {
                 float v[32];
                 tmem_ld32(tcol + c0, v);
-                if (j_fast && a.vec_out) {
+                if (a.tma_out) {
+                    // the box goes to C by one TMA store, which clips the rows
+                    // past M and the columns past J
+                    if (nrows > 0 && c0 < a.J) {
+                        if (lane == 0) bulk_wait_read();   // the previous store has read the box
+                        __syncwarp();
+                        if (a.variant == V_COL) {
+                            // [column][row]: rows contiguous in C
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) box[j * 32 + lane] = v[j];
+                        } else {
+                            // [row][column], 16-byte chunks placed the way the
+                            // map's 128-byte swizzle reads them (conflict-free)
+                            float4* b4 = reinterpret_cast<float4*>(box);
+#pragma unroll
+                            for (int c = 0; c < 8; ++c)
+                                b4[lane * 8 + (c ^ (lane & 7))] =
+                                    make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                        }
+                        fence_proxy_async();
+                        __syncwarp();
+                        if (lane == 0) {
+                            if (a.variant == V_COL) tma_store_3d(&cmap, (int)rbase, c0, (int)o, box_addr);
+                            else tma_store_2d(&cmap, c0, (int)rbase, box_addr);
+                            bulk_commit();
+                        }
+                    }
+                } else if (j_fast && a.vec_out) {
                     // 32 x 32 tile with 16-byte chunks XOR-swizzled by row: both the
                     // row-wise writes and the chunk-wise reads are conflict-free
                     float4* t4 = reinterpret_cast<float4*>(tile);
@@ -616,19 +657,24 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
                     }
                     __syncwarp();
                 } else if (a.vec_rows) {
-                    // rows contiguous in C: a 4 x 4 transpose among lanes 4g..4g+3
-                    // turns four rows x four columns into one 16-byte vector of
-                    // four rows per lane; eight lanes write 128 contiguous bytes
-                    const int g = lane >> 2, jj = lane & 3;
-                    const int64_t r0 = rbase + 4 * g;
-                    const int64_t nr = a.M - r0;              // rows of this vector that exist
+                    // rows contiguous in C: the warp's 32 rows x 32 columns go
+                    // through its shared-memory tile as [column][row] (32
+                    // conflict-free 4-byte stores per lane); each quarter-warp
+                    // then reads one column's 32 rows (8 x 16 bytes, conflict
+                    // free) and writes them as 128 contiguous bytes of C
 #pragma unroll
-                    for (int c = 0; c < 32; c += 4) {
-                        float4 x = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
-                        transpose4(x, jj);
-                        const int jg = c0 + c + jj;
+                    for (int j = 0; j < 32; ++j) tile[j * 32 + lane] = v[j];
+                    __syncwarp();
+                    const int g = lane & 7, jj = lane >> 3;     // rows 4g..4g+3 of column 4*it+jj
+                    const int64_t nr = a.M - (rbase + 4 * g);   // rows of this vector that exist
+                    float* const pbase = a.C + obase + rbase + 4 * g;
+#pragma unroll
+                    for (int it = 0; it < 8; ++it) {
+                        const int col = 4 * it + jj;
+                        const int jg = c0 + col;
+                        float4 x = *reinterpret_cast<const float4*>(tile + col * 32 + 4 * g);
                         if (jg < a.J && nr > 0) {
-                            float* p = a.C + obase + r0 + (int64_t)jg * a.scq;
+                            float* p = pbase + (int64_t)jg * a.scq;
                             if (nr >= 4) {
                                 float4* p4 = reinterpret_cast<float4*>(p);
                                 if (a.accumulate) {
@@ -642,6 +688,7 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
                             }
                         }
                     }
+                    __syncwarp();
                 } else if (lane < nrows) {
                     float* pc = a.C + obase + (rbase + lane) * a.sc_m;
 #pragma unroll
@@ -658,6 +705,7 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
             mbar_arrive(bars.acc_empty + 8 * acc.idx);
             acc.next(a.nacc);
         }
+        if (a.tma_out && lane == 0) bulk_wait_all();
     }
 
     tc_fence_before();
@@ -766,6 +814,20 @@ Layout layout_for(const TtmPlan& P)
         if (L.ns_stg > 8) L.ns_stg = 8;
         if (L.ns_stg >= 2) break;
     }
+    // Depth of the A ring. Where C is about as large as A (J >= n_q), more
+    // than about 64 KB of A in flight per SM lowers the DRAM throughput (the
+    // reads crowd out the write-back of C: on 128^4, 96^4 and 64^5 FP32
+    // tensors 4 stages run at 6.2-6.9 TB/s, 5-8 stages at 5.3-6.4); the less
+    // of C there is per byte of A, the deeper the ring pays (J = n_q / 4 and
+    // n_q / 8 run fastest with 6-8 stages). COL tiles past a short inner
+    // extent load only the rows that exist, so their stages hold fewer bytes.
+    {
+        int want = 4;
+        if (P.J < P.nq) want += (int)(4 * (P.nq - P.J) / P.nq);
+        const int64_t rows = P.tc_variant == V_COL && P.rows.d[0].n < BM ? P.rows.d[0].n : BM;
+        want = (int)((want * BM + rows - 1) / rows);
+        if (L.ns_stg > want) L.ns_stg = want < 2 ? 2 : want;
+    }
     L.off_stg = 0;
     L.off_op = L.ns_stg * L.a_stage;
     L.off_b = L.off_op + L.ns_op * L.op_stage;
@@ -855,6 +917,39 @@ int launch_prec(const TtmPlan& P, const void* A, const void* B, void* C, int acc
     }
     if (cr != CUDA_SUCCESS) return TL_EUNSUPPORTED;
 
+    // C by TMA stores where its layout allows a tensor map: 16-byte aligned
+    // base and strides, coordinates in 32 bits; otherwise the warps store
+    CUtensorMap cmap{};
+    a.tma_out = 0;
+    if (!accumulate && (reinterpret_cast<uintptr_t>(C) % 16) == 0 && (L.off_epi % 1024) == 0 &&
+        P.J < (1LL << 31) && a.M < (1LL << 31)) {
+        if (P.tc_variant == V_ROW && P.scq == 1) {
+            const int64_t ld = a.M > 1 ? a.sc_m : (P.J + 3) / 4 * 4;
+            if (ld % 4 == 0 && ld > 0 && ld * 4 < (1LL << 40)) {
+                const cuuint64_t gdim[2] = {(cuuint64_t)P.J, (cuuint64_t)a.M};
+                const cuuint64_t gstr[1] = {(cuuint64_t)ld * 4};
+                const cuuint32_t box[2] = {32, 32};
+                a.tma_out = enc(&cmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, gdim, gstr, box, estr,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            }
+        } else if (P.tc_variant == V_COL && a.sc_m == 1) {
+            const int64_t outer = a.ntiles / a.tiles_per_o;
+            const int64_t so = outer > 1 ? a.sc_o : P.scq * P.J;
+            if (P.scq % 4 == 0 && P.scq > 0 && so % 4 == 0 && so > 0 && outer < (1LL << 31) &&
+                P.scq * 4 < (1LL << 40) && so * 4 < (1LL << 40)) {
+                const cuuint64_t gdim[3] = {(cuuint64_t)a.M, (cuuint64_t)P.J, (cuuint64_t)outer};
+                const cuuint64_t gstr[2] = {(cuuint64_t)P.scq * 4, (cuuint64_t)so * 4};
+                const cuuint32_t box[3] = {32, 32, 1};
+                a.tma_out = enc(&cmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, C, gdim, gstr, box, estr,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            }
+        }
+    }
+
     // converted B in the per-stream workspace
     const size_t img_bytes = (size_t)L.nks * L.nparts * L.opb_part;
     uint8_t* img = static_cast<uint8_t*>(workspace(st, img_bytes));
@@ -875,7 +970,7 @@ int launch_prec(const TtmPlan& P, const void* A, const void* B, void* C, int acc
                              227 * 1024);
     });
     int grid = (int)(a.ntiles < sms ? a.ntiles : sms);
-    ttm_tc_kernel<PREC><<<grid, kThreads, L.smem, st>>>(map, a);
+    ttm_tc_kernel<PREC><<<grid, kThreads, L.smem, st>>>(map, cmap, a);
     return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
 }
 
