@@ -129,3 +129,50 @@ def test_tc_full_scale_sampled(tl, cuda_dev, scale_tensors, prec):
             ref = oracle.ttm_at(mem, n, wA, q, Bm.reshape(-1), 128, 1, idx)
             assert rel_err(got[tuple(idx.T)], ref) <= TOL[prec], (pi, q)
     assert tl.tl_device_status() == tl.TL_OK
+
+
+# The epilogue's store paths: TMA stores of 32 x 32 boxes where C's base and
+# strides are 16-byte aligned and nothing accumulates; warp stores otherwise
+# (16-byte vectors through a shared-memory transpose, or single elements).
+STORE_CASES = [
+    # (shape, q, J, C offset in elements, accumulate)
+    ((64, 33, 17), 1, 37, 0, False),     # ROW, C rows 37 apart: single elements
+    ((200, 48, 3), 2, 37, 0, False),     # COL, TMA boxes clipped at 37 columns
+    ((64, 33, 17), 1, 40, 1, False),     # ROW, C base not 16-byte aligned: single elements
+    ((200, 48, 3), 2, 40, 1, False),     # COL, C base not 16-byte aligned: single elements
+    ((200, 48, 3), 2, 40, 0, True),      # COL, accumulate: vectors along rows
+    ((64, 33, 17), 1, 40, 0, True),      # ROW, accumulate: vectors along j
+    ((200, 48, 3), 2, 40, 0, False),     # COL, TMA stores (rows past 200 clipped)
+    ((64, 33, 17), 1, 40, 0, False),     # ROW, TMA stores (columns past 40 clipped)
+]
+
+
+@pytest.mark.parametrize("prec", sorted(PREC))
+@pytest.mark.parametrize("case", range(len(STORE_CASES)))
+def test_tc_store_paths_bit_exact(tl, cuda_dev, prec, case):
+    n, q, J, off, acc = STORE_CASES[case]
+    X = synth.integers(n, 6700 + case)
+    Bm = synth.integers((J, n[q - 1]), 6710 + case)
+    nout = tuple(J if r == q - 1 else x for r, x in enumerate(n))
+    NC = int(np.prod(nout))
+    C0 = synth.integers(nout, 6720 + case) if acc else np.zeros(nout)
+    A = put(X, (1, 2, 3), cuda_dev, "f32")
+    Bt = to_dev(np.ascontiguousarray(Bm).reshape(-1), cuda_dev, "f32")
+    # C at element offset `off` inside a buffer whose other elements hold a sentinel
+    buf = torch.full((NC + off + 5,), -7.0, dtype=torch.float32, device=cuda_dev)
+    buf[off:off + NC] = torch.from_numpy(synth.to_memory(np.asarray(C0, np.float32),
+                                                         (1, 2, 3))).to(cuda_dev)
+    Cv = buf[off:off + NC]
+    P = plan_kernel(tl, A, n, (1, 2, 3), q, J, Cv, PREC[prec])
+    assert P["kernel"] == "ttm_tc", P
+    rc = tl.tl_ttm(tl.Desc(A, n), Bt, J, n[q - 1], 1, q, tl.Desc(Cv, nout), PREC[prec], int(acc))
+    tl.check(rc, "tl_ttm")
+    torch.cuda.synchronize()
+    out = buf.cpu().numpy()
+    ref = oracle.ttm(synth.to_memory(X, (1, 2, 3)), n, oracle.strides(n), q,
+                     np.ascontiguousarray(Bm).reshape(-1), J, n[q - 1], 1,
+                     C=synth.to_memory(np.asarray(C0, np.float64), (1, 2, 3)),
+                     wC=oracle.strides(nout), accumulate=acc)
+    np.testing.assert_array_equal(out[off:off + NC], ref)
+    assert np.all(out[:off] == -7.0) and np.all(out[off + NC:] == -7.0)
+    assert tl.tl_device_status() == tl.TL_OK
