@@ -10,16 +10,18 @@
 //   COL  the fastest output mode i has unit stride in A and w_q > 1: the
 //        rows of one tile are 128 consecutive i of one outer index o, loaded
 //        by a 3-D TMA box of 128 i x 32 k x 1 o.
-// FP32 data is converted on chip: four converter warps read the FP32 tile,
+// FP32 data is converted on chip: eight converter warps read the FP32 tile,
 // round it to TF32, to BF16, or split it into BF16 hi + lo (hi = RN(a),
 // lo = RN(a - hi)), and write the tensor-core operand in the K-major,
 // no-swizzle canonical layout (8-row x 16-byte core matrices).  B is
-// converted once per call into the same layout in global scratch and
-// streamed per k stage with bulk copies.  Split-BF16x3 issues
-// hi*hi + hi*lo + lo*hi; every product accumulates in FP32 in TMEM.
+// converted once per call into the same layout in global scratch; up to
+// 64 KB of it stays in shared memory for the whole launch, a larger one is
+// streamed per k stage with bulk copies issued by converter thread 0.
+// Split-BF16x3 issues hi*hi + hi*lo + lo*hi; every product accumulates in
+// FP32 in TMEM.
 //
 // Warp roles (576 threads, one CTA per SM, persistent over tiles):
-//   warp 0       TMA producer (one thread)
+//   warp 0       TMA producer of the FP32 A tiles (one thread)
 //   warp 1       TMEM allocator and MMA issuer (one thread)
 //   warps 2-9    converters: two threads per operand row, each converting
 //                half of the stage's 32 k values
@@ -382,10 +384,10 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
     if (warp == 0) {
         // ------------------------------------------------------ producer
         if (lane == 0) {
-            Pipe st, op;
+            Pipe st;
             bool ok = true;
             // parity of the last arm of each stage, to drain on exit
-            uint32_t stg_armed = 0, stg_par = 0, op_armed = 0, op_par = 0;
+            uint32_t stg_armed = 0, stg_par = 0;
             if (a.b_resident) {
                 // the whole converted B, once per CTA, in 64 KB pieces
                 mbar_arrive_tx(bars.b_full, a.b_bytes);
@@ -414,18 +416,6 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
                     stg_armed |= 1u << st.idx;
                     stg_par = (stg_par & ~(1u << st.idx)) | (st.phase << st.idx);
                     st.next(a.ns_stg);
-                    if (a.b_resident) continue;
-
-                    if (!(ok = mbar_wait(bars.op_empty + 8 * op.idx, op.phase ^ 1u))) break;
-                    uint32_t ob = bars.op_full + 8 * op.idx;
-                    mbar_arrive_tx(ob, kParts * a.opb_part_bytes);
-                    for (int part = 0; part < kParts; ++part)
-                        bulk_load(op_b(op.idx, part),
-                                  a.bimg + ((size_t)ks * kParts + part) * a.opb_part_bytes,
-                                  a.opb_part_bytes, ob);
-                    op_armed |= 1u << op.idx;
-                    op_par = (op_par & ~(1u << op.idx)) | (op.phase << op.idx);
-                    op.next(a.ns_op);
                 }
             }
             if (!ok || a.b_resident) {
@@ -441,12 +431,6 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
                     if (stg_armed & (1u << s)) {
                         long long t0 = clock64();
                         while (!mbar_try(bars.stg_full + 8 * s, (stg_par >> s) & 1u) &&
-                               clock64() - t0 < kTimeoutCycles) {}
-                    }
-                for (int s = 0; s < a.ns_op; ++s)
-                    if (op_armed & (1u << s)) {
-                        long long t0 = clock64();
-                        while (!mbar_try(bars.op_full + 8 * s, (op_par >> s) & 1u) &&
                                clock64() - t0 < kTimeoutCycles) {}
                     }
             }
@@ -502,8 +486,24 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
         constexpr int KH = BK / 2;
         Pipe st, op;
         bool ok = true;
+        // a streamed B is copied by converter thread 0 into each operand stage
+        // as the stage frees up, so the A producer never waits on the operand
+        // ring and keeps the whole staging ring in flight
+        const bool b_loader = !a.b_resident && tc == 0;
+        uint32_t op_armed = 0, op_par = 0;   // stages with a B copy in flight (for the drain)
         for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
             for (int ks = 0; ks < a.nks && ok; ++ks) {
+                if (b_loader) {
+                    if (!(ok = mbar_wait(bars.op_empty + 8 * op.idx, op.phase ^ 1u))) break;
+                    const uint32_t ob = bars.op_full + 8 * op.idx;
+                    mbar_arrive_tx(ob, kParts * a.opb_part_bytes);
+                    for (int part = 0; part < kParts; ++part)
+                        bulk_load(op_b(op.idx, part),
+                                  a.bimg + ((size_t)ks * kParts + part) * a.opb_part_bytes,
+                                  a.opb_part_bytes, ob);
+                    op_armed |= 1u << op.idx;
+                    op_par = (op_par & ~(1u << op.idx)) | (op.phase << op.idx);
+                }
                 if (!(ok = mbar_wait(bars.stg_full + 8 * st.idx, st.phase))) break;
                 if (!(ok = mbar_wait(bars.op_empty + 8 * op.idx, op.phase ^ 1u))) break;
                 const float* stg = reinterpret_cast<const float*>(
@@ -561,6 +561,15 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
                 st.next(a.ns_stg);
                 op.next(a.ns_op);
             }
+        }
+        if (!ok && b_loader) {
+            // drain: every B copy issued must land before the CTA exits
+            for (int s2 = 0; s2 < a.ns_op; ++s2)
+                if (op_armed & (1u << s2)) {
+                    long long t0 = clock64();
+                    while (!mbar_try(bars.op_full + 8 * s2, (op_par >> s2) & 1u) &&
+                           clock64() - t0 < kTimeoutCycles) {}
+                }
         }
     } else {
         // ------------------------------------------------------ epilogue
