@@ -1021,6 +1021,27 @@ def link_rates(torch, dst, src, stream, reps=3):
     return rates
 
 
+def duplex_rate(torch, d_dst, d_src, h_dst, h_src, s_d2h, s_h2d, stream):
+    """Aggregate GB/s of a device-to-host and a host-to-device copy started
+    together on two streams: both copies' bytes over the time until the
+    later one ends (best of 3)."""
+    best = 0.0
+    nbytes = d_src.numel() * d_src.element_size() + h_src.numel() * h_src.element_size()
+    for _ in range(3):
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for st, dst, src in ((s_d2h, d_dst, d_src), (s_h2d, h_dst, h_src)):
+            st.wait_event(t0)
+            with torch.cuda.stream(st):
+                dst.copy_(src, non_blocking=True)
+        stream.wait_stream(s_d2h)
+        stream.wait_stream(s_h2d)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, nbytes / (t0.elapsed_time(t1) / 1e3) / 1e9)
+    return best
+
+
 def measure_e2e(tl, torch, wl, args, sh, world, barrier):
     """The same 17 calls through the C ABI with every input copied from pinned
     host memory and every output copied back inside the timed region.
@@ -1150,6 +1171,14 @@ def measure_e2e(tl, torch, wl, args, sh, world, barrier):
     bound_ms = max(d2h / (link["d2h_GB/s"] * 1e9), h2d / (link["h2d_GB/s"] * 1e9)) * 1e3
     link["bound_ms_per_step"] = round(bound_ms, 3)
     link["frac"] = round(bound_ms / (ms / steps), 3)
+    # both directions at once, as the pipeline runs them: the step's bytes at
+    # the measured duplex rate are a second, tighter bound where the link's
+    # two directions share bandwidth
+    link["duplex_GB/s"] = round(duplex_rate(torch, oM, outs[-1], sets[0]["AF"], hF, s_out, s_in,
+                                            compute), 1)
+    bound_dup = max(bound_ms, (d2h + h2d) / (link["duplex_GB/s"] * 1e9) * 1e3)
+    link["bound_ms_per_step_duplex"] = round(bound_dup, 3)
+    link["frac_duplex"] = round(bound_dup / (ms / steps), 3)
     return {"value": round(job_throughput(wl.step_bytes, world, steps, ms), 2), "unit": "GB/s",
             "last_output_matches_device_run": same,
             "ms_per_step": round(ms / steps, 3), "steps": steps,
