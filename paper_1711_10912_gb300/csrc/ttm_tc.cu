@@ -16,17 +16,18 @@
 // no-swizzle canonical layout (8-row x 16-byte core matrices).  B is
 // converted once per call into the same layout in global scratch; up to
 // 64 KB of it stays in shared memory for the whole launch, a larger one is
-// streamed per k stage with bulk copies issued by converter thread 0.
+// streamed per k stage with bulk copies by a warp of its own.
 // Split-BF16x3 issues hi*hi + hi*lo + lo*hi; every product accumulates in
 // FP32 in TMEM.
 //
-// Warp roles (576 threads, one CTA per SM, persistent over tiles):
+// Warp roles (608 threads, one CTA per SM, persistent over tiles):
 //   warp 0       TMA producer of the FP32 A tiles (one thread)
 //   warp 1       TMEM allocator and MMA issuer (one thread)
 //   warps 2-9    converters: two threads per operand row, each converting
 //                half of the stage's 32 k values
 //   warps 10-17  epilogue: TMEM -> registers -> C; warp w reads the TMEM
 //                lane quarter w % 4 and every other 32-column chunk
+//   warp 18      B stream (one thread; idle when B is resident)
 // Eight + eight warps rather than four + four: the conversion and drain
 // chains are latency-bound, and more warps in flight keep the HBM stream
 // busy (measured on GB300).
@@ -58,7 +59,8 @@ constexpr int kEpiWarps = 8;
 constexpr int kConvThreads = 32 * kConvWarps;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kEpiWarp0 = 2 + kConvWarps;
-constexpr int kThreads = 32 * (2 + kConvWarps + kEpiWarps);
+constexpr int kBWarp = kEpiWarp0 + kEpiWarps;   // streams B when it is not resident
+constexpr int kThreads = 32 * (kBWarp + 1);
 constexpr int kTmemCols = 512;
 constexpr long long kTimeoutCycles = 4000000000LL;   // about 2 s at 2 GHz
 
@@ -486,24 +488,8 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
         constexpr int KH = BK / 2;
         Pipe st, op;
         bool ok = true;
-        // a streamed B is copied by converter thread 0 into each operand stage
-        // as the stage frees up, so the A producer never waits on the operand
-        // ring and keeps the whole staging ring in flight
-        const bool b_loader = !a.b_resident && tc == 0;
-        uint32_t op_armed = 0, op_par = 0;   // stages with a B copy in flight (for the drain)
         for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
             for (int ks = 0; ks < a.nks && ok; ++ks) {
-                if (b_loader) {
-                    if (!(ok = mbar_wait(bars.op_empty + 8 * op.idx, op.phase ^ 1u))) break;
-                    const uint32_t ob = bars.op_full + 8 * op.idx;
-                    mbar_arrive_tx(ob, kParts * a.opb_part_bytes);
-                    for (int part = 0; part < kParts; ++part)
-                        bulk_load(op_b(op.idx, part),
-                                  a.bimg + ((size_t)ks * kParts + part) * a.opb_part_bytes,
-                                  a.opb_part_bytes, ob);
-                    op_armed |= 1u << op.idx;
-                    op_par = (op_par & ~(1u << op.idx)) | (op.phase << op.idx);
-                }
                 if (!(ok = mbar_wait(bars.stg_full + 8 * st.idx, st.phase))) break;
                 if (!(ok = mbar_wait(bars.op_empty + 8 * op.idx, op.phase ^ 1u))) break;
                 const float* stg = reinterpret_cast<const float*>(
@@ -562,14 +548,38 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
                 op.next(a.ns_op);
             }
         }
-        if (!ok && b_loader) {
-            // drain: every B copy issued must land before the CTA exits
-            for (int s2 = 0; s2 < a.ns_op; ++s2)
-                if (op_armed & (1u << s2)) {
-                    long long t0 = clock64();
-                    while (!mbar_try(bars.op_full + 8 * s2, (op_par >> s2) & 1u) &&
-                           clock64() - t0 < kTimeoutCycles) {}
+    } else if (warp == kBWarp) {
+        // ------------------------------------------------------ B stream
+        // a B too large to stay resident is copied into each operand stage as
+        // soon as the tensor cores free it, ahead of the conversion of that
+        // stage, so neither the A producer nor the converters wait on it
+        if (lane == 0 && !a.b_resident) {
+            Pipe op;
+            bool ok = true;
+            uint32_t op_armed = 0, op_par = 0;   // stages with a copy in flight (for the drain)
+            for (int64_t tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+                for (int ks = 0; ks < a.nks && ok; ++ks) {
+                    if (!(ok = mbar_wait(bars.op_empty + 8 * op.idx, op.phase ^ 1u))) break;
+                    const uint32_t ob = bars.op_full + 8 * op.idx;
+                    mbar_arrive_tx(ob, kParts * a.opb_part_bytes);
+                    for (int part = 0; part < kParts; ++part)
+                        bulk_load(op_b(op.idx, part),
+                                  a.bimg + ((size_t)ks * kParts + part) * a.opb_part_bytes,
+                                  a.opb_part_bytes, ob);
+                    op_armed |= 1u << op.idx;
+                    op_par = (op_par & ~(1u << op.idx)) | (op.phase << op.idx);
+                    op.next(a.ns_op);
                 }
+            }
+            if (!ok) {
+                // drain: every copy issued must land before the CTA exits
+                for (int s2 = 0; s2 < a.ns_op; ++s2)
+                    if (op_armed & (1u << s2)) {
+                        long long t0 = clock64();
+                        while (!mbar_try(bars.op_full + 8 * s2, (op_par >> s2) & 1u) &&
+                               clock64() - t0 < kTimeoutCycles) {}
+                    }
+            }
         }
     } else {
         // ------------------------------------------------------ epilogue
