@@ -31,8 +31,8 @@
 // Eight + eight warps rather than four + four: the conversion and drain
 // chains are latency-bound, and more warps in flight keep the HBM stream
 // busy (measured on GB300).
-// Every mbarrier wait is bounded: after about a second without progress the
-// thread records a timeout in a status word, the CTA drains its TMA copies,
+// Every mbarrier wait is bounded: after about two seconds without progress
+// the thread records a timeout in a status word, the CTA drains its TMA copies,
 // frees its TMEM and returns, and tl_device_status() reports TL_ETIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -44,6 +44,7 @@
 #include <mutex>
 
 #include "kernels.h"
+#include "pipeline.cuh"
 #include "runtime.h"
 
 namespace tl {
@@ -62,59 +63,29 @@ constexpr int kEpiWarp0 = 2 + kConvWarps;
 constexpr int kBWarp = kEpiWarp0 + kEpiWarps;   // streams B when it is not resident
 constexpr int kThreads = 32 * (kBWarp + 1);
 constexpr int kTmemCols = 512;
-constexpr long long kTimeoutCycles = 4000000000LL;   // about 2 s at 2 GHz
 
 enum Variant { V_NONE = 0, V_ROW = 1, V_COL = 2 };
 
 // ------------------------------------------------------------ PTX helpers --
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
+// mbarriers, bulk copies, TMA loads and proxy fences come from pipeline.cuh;
+// this kernel's bounded waits report into g_tc_status.
+using pipe::bulk_load;
+using pipe::fence_proxy_async;
+using pipe::kTimeoutCycles;
+using pipe::mbar_arrive;
+using pipe::mbar_arrive_tx;
+using pipe::mbar_init;
+using pipe::mbar_try;
+using pipe::smem_u32;
+using pipe::tma_load_2d;
+using pipe::tma_load_3d;
 
 // Bounded wait: false (and the status word set) after `limit` SM cycles.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
                                           long long limit = kTimeoutCycles)
 {
-    if (mbar_try(bar, parity)) return true;
-    long long t0 = clock64();
-    while (!mbar_try(bar, parity)) {
-        if (clock64() - t0 > limit) {
-            atomicOr(&g_tc_status, 1u);
-            return false;
-        }
-    }
-    return true;
+    return pipe::mbar_wait(bar, parity, &g_tc_status, limit);
 }
 
 // One thread waits on a barrier whose phase never completes (its arrival
@@ -129,39 +100,6 @@ __global__ void selftest_wait_kernel(long long limit)
         mbar_arrive(b);
         mbar_wait(b, 0u, limit);
     }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            int z, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // TMA stores of a shared-memory box into C (bulk-group completion, issued and
