@@ -404,10 +404,12 @@ int tl_plan_describe(int32_t op, const tl_tensor* A_, const tl_tensor* B_, uint3
         std::snprintf(b, sizeof b,
                       "{\"op\":\"ttm\",\"kernel\":\"%s\",\"precision\":%d,\"nq\":%lld,"
                       "\"saq\":%lld,\"J\":%lld,\"scq\":%lld,\"M\":%lld,\"tc_variant\":%d,"
-                      "\"splits\":%lld,\"dims\":",
+                      "\"splits\":%lld,",
                       kernel_name(P.kernel), P.precision, (long long)P.nq, (long long)P.saq,
                       (long long)P.J, (long long)P.scq, (long long)P.M, P.tc_variant, splits);
         s = b;
+        if (P.kernel == K_TTM_TC) s += "\"tc\":" + ttm_tc_describe(P, C.data) + ",";
+        s += "\"dims\":";
         append_space(s, P.rows);
         s += "}";
     } else if (op == TL_OP_ENTRYWISE) {

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "plan.h"
 
 namespace tl {
@@ -44,6 +46,10 @@ int launch_ttm_tc(const TtmPlan& P, const void* A, const void* B, void* C, int a
                   int num_sms, cudaStream_t st);
 // kernels one launch_ttm_tc call enqueues
 int ttm_tc_launches(const TtmPlan& P);
+// JSON object with the tensor-core kernel's launch configuration for P and an
+// output at C (host only: ring depths, B residency, shared memory, threads,
+// whether C is written by TMA stores)
+std::string ttm_tc_describe(const TtmPlan& P, const void* C);
 // TL_ETIMEOUT if a bounded wait in a tensor-core kernel gave up since the
 // last cleared check, else TL_OK (reads the device status word).
 int ttm_tc_status(bool clear);

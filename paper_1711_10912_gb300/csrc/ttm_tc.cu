@@ -41,7 +41,9 @@
 
 #include <atomic>
 #include <cstdint>
+#include <cstdio>
 #include <mutex>
+#include <string>
 
 #include "kernels.h"
 #include "pipeline.cuh"
@@ -797,6 +799,51 @@ Layout layout_for(const TtmPlan& P)
     return L;
 }
 
+// The tensor map C is written through when the epilogue stores by TMA: 16-byte
+// aligned base and strides, coordinates in 32 bits, no accumulation (a TMA
+// store overwrites).  ROW: 2-D {J, M}, 32 x 32 boxes with 128-byte swizzle;
+// COL: 3-D {inner, J, outer}, 32 x 32 x 1 boxes.
+struct StoreMap {
+    bool ok = false;
+    int rank = 0;
+    cuuint64_t gdim[3] = {0, 0, 0}, gstr[2] = {0, 0};
+    cuuint32_t box[3] = {32, 32, 1};
+};
+
+StoreMap store_map(const TtmPlan& P, const Layout& L, const void* C, int accumulate)
+{
+    StoreMap m;
+    if (accumulate || (reinterpret_cast<uintptr_t>(C) % 16) != 0 || (L.off_epi % 1024) != 0 ||
+        P.J >= (1LL << 31))
+        return m;
+    if (P.tc_variant == V_ROW && P.scq == 1) {
+        const int64_t M = P.M, sc_m = P.rows.nd ? P.rows.d[0].s[1] : 0;
+        const int64_t ld = M > 1 ? sc_m : (P.J + 3) / 4 * 4;
+        if (M < (1LL << 31) && ld % 4 == 0 && ld > 0 && ld * 4 < (1LL << 40)) {
+            m.rank = 2;
+            m.gdim[0] = (cuuint64_t)P.J;
+            m.gdim[1] = (cuuint64_t)M;
+            m.gstr[0] = (cuuint64_t)ld * 4;
+            m.ok = true;
+        }
+    } else if (P.tc_variant == V_COL && P.rows.d[0].s[1] == 1) {
+        const int64_t inner = P.rows.d[0].n;
+        const int64_t outer = P.rows.nd == 2 ? P.rows.d[1].n : 1;
+        const int64_t so = outer > 1 ? P.rows.d[1].s[1] : P.scq * P.J;
+        if (inner < (1LL << 31) && outer < (1LL << 31) && P.scq % 4 == 0 && P.scq > 0 &&
+            so % 4 == 0 && so > 0 && P.scq * 4 < (1LL << 40) && so * 4 < (1LL << 40)) {
+            m.rank = 3;
+            m.gdim[0] = (cuuint64_t)inner;
+            m.gdim[1] = (cuuint64_t)P.J;
+            m.gdim[2] = (cuuint64_t)outer;
+            m.gstr[0] = (cuuint64_t)P.scq * 4;
+            m.gstr[1] = (cuuint64_t)so * 4;
+            m.ok = true;
+        }
+    }
+    return m;
+}
+
 template <int PREC>
 int launch_prec(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate, int sms,
                 cudaStream_t st)
@@ -874,38 +921,17 @@ int launch_prec(const TtmPlan& P, const void* A, const void* B, void* C, int acc
     }
     if (cr != CUDA_SUCCESS) return TL_EUNSUPPORTED;
 
-    // C by TMA stores where its layout allows a tensor map: 16-byte aligned
-    // base and strides, coordinates in 32 bits; otherwise the warps store
+    // C by TMA stores where its layout allows a tensor map; otherwise the
+    // warps store
     CUtensorMap cmap{};
     a.tma_out = 0;
-    if (!accumulate && (reinterpret_cast<uintptr_t>(C) % 16) == 0 && (L.off_epi % 1024) == 0 &&
-        P.J < (1LL << 31) && a.M < (1LL << 31)) {
-        if (P.tc_variant == V_ROW && P.scq == 1) {
-            const int64_t ld = a.M > 1 ? a.sc_m : (P.J + 3) / 4 * 4;
-            if (ld % 4 == 0 && ld > 0 && ld * 4 < (1LL << 40)) {
-                const cuuint64_t gdim[2] = {(cuuint64_t)P.J, (cuuint64_t)a.M};
-                const cuuint64_t gstr[1] = {(cuuint64_t)ld * 4};
-                const cuuint32_t box[2] = {32, 32};
-                a.tma_out = enc(&cmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, gdim, gstr, box, estr,
-                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-            }
-        } else if (P.tc_variant == V_COL && a.sc_m == 1) {
-            const int64_t outer = a.ntiles / a.tiles_per_o;
-            const int64_t so = outer > 1 ? a.sc_o : P.scq * P.J;
-            if (P.scq % 4 == 0 && P.scq > 0 && so % 4 == 0 && so > 0 && outer < (1LL << 31) &&
-                P.scq * 4 < (1LL << 40) && so * 4 < (1LL << 40)) {
-                const cuuint64_t gdim[3] = {(cuuint64_t)a.M, (cuuint64_t)P.J, (cuuint64_t)outer};
-                const cuuint64_t gstr[2] = {(cuuint64_t)P.scq * 4, (cuuint64_t)so * 4};
-                const cuuint32_t box[3] = {32, 32, 1};
-                a.tma_out = enc(&cmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, C, gdim, gstr, box, estr,
-                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-            }
-        }
-    }
+    const StoreMap sm = store_map(P, L, C, accumulate);
+    if (sm.ok)
+        a.tma_out = enc(&cmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sm.rank, C, sm.gdim, sm.gstr, sm.box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        sm.rank == 2 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 
     // converted B in the per-stream workspace
     const size_t img_bytes = (size_t)L.nks * L.nparts * L.opb_part;
@@ -934,6 +960,18 @@ int launch_prec(const TtmPlan& P, const void* A, const void* B, void* C, int acc
 }  // namespace
 
 int ttm_tc_launches(const TtmPlan&) { return 2; }
+
+std::string ttm_tc_describe(const TtmPlan& P, const void* C)
+{
+    const Layout L = layout_for(P);
+    const StoreMap sm = store_map(P, L, C, 0);
+    char b[256];
+    std::snprintf(b, sizeof b,
+                  "{\"a_stages\":%d,\"op_stages\":%d,\"b_resident\":%d,\"smem\":%u,"
+                  "\"threads\":%d,\"store\":\"%s\"}",
+                  L.ns_stg, L.ns_op, L.b_resident, L.smem, kThreads, sm.ok ? "tma" : "warps");
+    return b;
+}
 
 int launch_ttm_tc(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate,
                   int num_sms, cudaStream_t st)

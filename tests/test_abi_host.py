@@ -239,3 +239,52 @@ def test_view_rejects_bad_ranges(tl):
     assert tl.tl_view(A, (0, 0, 0), (0, 1, 1), (3, 1, 2))[0] == tl.TL_EINVAL   # t < 1
     assert tl.tl_view(A, (2, 0, 0), (1, 1, 1), (1, 1, 2))[0] == tl.TL_EINVAL   # f > l
     assert tl.tl_view(A, (0, 0, 0), (1, 1, 1), (4, 1, 2))[0] == tl.TL_EINVAL   # l >= n
+
+
+# ------------------------------------------ tensor-core ttm launch configuration
+
+def _tc_config(tl, n, q, J, prec=5, pi=None, c_addr=FAKE * 8192, c_pi=None):
+    nout = tuple(J if r == q - 1 else x for r, x in enumerate(n))
+    rc, P = _plan(tl, tl.TL_OP_TTM, _desc(tl, n, pi, addr=FAKE * 4096),
+                  _desc(tl, nout, c_pi if c_pi else pi, addr=c_addr), q=q, J=J, prec=prec)
+    assert rc == 0 and P["kernel"] == "ttm_tc", P
+    return P["tc"]
+
+
+def test_tc_ring_depth_follows_the_write_share(tl):
+    # C as large as A (J = n_q): 4 stages of A in flight per SM, every mode
+    for q in (1, 2, 3, 4):
+        cfg = _tc_config(tl, (128,) * 4, q, 128)
+        assert cfg["a_stages"] == 4 and cfg["b_resident"] == 1, (q, cfg)
+    # J = n_q / 4: 4 + 4 * (128 - 32) / 128 = 7 stages
+    assert _tc_config(tl, (128,) * 4, 2, 32)["a_stages"] == 7
+    # COL tiles of 96 valid rows hold fewer bytes: 4 * 128 / 96 -> 6 stages
+    assert _tc_config(tl, (96,) * 4, 2, 96)["a_stages"] == 6
+    # 64-row COL tiles: 8
+    assert _tc_config(tl, (64,) * 5, 2, 64)["a_stages"] == 8
+
+
+def test_tc_configuration_fits_the_sm(tl):
+    for n, q, J, prec in [((128,) * 4, 1, 128, 5), ((512, 512, 512), 1, 512, 5),
+                          ((512, 512, 512), 3, 512, 3), ((512, 512, 512), 1, 64, 4),
+                          ((64, 33, 17), 1, 300, 5), ((20, 152, 36), 1, 16, 3)]:
+        cfg = _tc_config(tl, n, q, J, prec)
+        assert cfg["smem"] <= 227 * 1024, (n, q, J, cfg)
+        assert cfg["a_stages"] >= 2 and cfg["op_stages"] >= 2, cfg
+        assert cfg["threads"] * 96 <= 65536      # 96 registers per thread fit the SM
+    # a converted B above 64 KB streams per k stage instead of staying resident
+    assert _tc_config(tl, (512, 512, 512), 1, 512)["b_resident"] == 0
+    assert _tc_config(tl, (128,) * 4, 1, 128, prec=3)["b_resident"] == 1   # TF32: 64 KB
+
+
+def test_tc_store_path_choice(tl):
+    n = (128,) * 4
+    # 16-byte aligned C with 16-byte strides: TMA stores, both orientations
+    assert _tc_config(tl, n, 1, 128)["store"] == "tma"
+    assert _tc_config(tl, n, 3, 128)["store"] == "tma"
+    # C not 16-byte aligned: the warps store
+    assert _tc_config(tl, n, 1, 128, c_addr=FAKE * 8192 + 4)["store"] == "warps"
+    assert _tc_config(tl, n, 3, 128, c_addr=FAKE * 8192 + 4)["store"] == "warps"
+    # ROW with C rows 37 elements apart: no tensor map
+    assert _tc_config(tl, (64, 33, 17), 1, 37)["store"] == "warps"
+    assert _tc_config(tl, (64, 33, 17), 1, 40)["store"] == "tma"
