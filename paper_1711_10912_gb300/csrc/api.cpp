@@ -9,6 +9,7 @@
 #include <mutex>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "kernels.h"
 #include "plan.h"
@@ -33,6 +34,29 @@ int device_sms()
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     if (dev >= 0 && dev < kMaxDevices) cache[dev].store(sms, std::memory_order_relaxed);
     return sms;
+}
+
+int smem_optin(const void* func, int bytes)
+{
+    struct Done {
+        int dev;
+        const void* func;
+        int bytes;
+    };
+    static std::mutex mu;
+    static std::vector<Done> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TL_ECUDA;
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Done& d : done)
+        if (d.dev == dev && d.func == func && d.bytes >= bytes) return TL_OK;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return TL_ECUDA;
+    }
+    done.push_back(Done{dev, func, bytes});
+    return TL_OK;
 }
 
 static std::atomic<uint64_t> g_launches{0};
@@ -409,6 +433,8 @@ int tl_plan_describe(int32_t op, const tl_tensor* A_, const tl_tensor* B_, uint3
                       (long long)P.J, (long long)P.scq, (long long)P.M, P.tc_variant, splits);
         s = b;
         if (P.kernel == K_TTM_TC) s += "\"tc\":" + ttm_tc_describe(P, C.data) + ",";
+        if (P.kernel == K_TTM_SIMT && P.dtype == TL_F32)
+            s += "\"sgemm\":" + ttm_sgemm_describe(P, A.data, C.data, splits > 1) + ",";
         s += "\"dims\":";
         append_space(s, P.rows);
         s += "}";

@@ -27,6 +27,16 @@ int ew_status(bool clear);
 int64_t ttm_simt_splits(const TtmPlan& P, int num_sms, int64_t* kchunk);
 size_t ttm_simt_workspace_bytes(const TtmPlan& P, int num_sms);
 int ttm_simt_launches(const TtmPlan& P, int num_sms);
+// FP32 register-tiled ttm (ttm_sgemm.cu): output tiles of the plan, and the
+// launch with `splits` k ranges of `kchunk` (splits > 1 writes the partial
+// sums to ws, which ttm_splitk_reduce adds into C).
+int64_t sgemm_tiles(const TtmPlan& P);
+// JSON object naming how the FP32 kernel reads A and B (k4: 16-byte vectors
+// along k, r4: along four contiguous rows, scalar) and writes C (j4, m4,
+// scalar; ws4 / ws1: split-K partials), for tl_plan_describe.
+std::string ttm_sgemm_describe(const TtmPlan& P, const void* A, const void* C, bool split);
+int launch_ttm_sgemm(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate,
+                     void* ws, int64_t splits, int64_t kchunk, int num_sms, cudaStream_t st);
 int launch_ttm_simt(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate,
                     void* ws, int num_sms, cudaStream_t st);
 

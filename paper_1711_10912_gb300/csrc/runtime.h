@@ -33,6 +33,11 @@ struct NvtxRange {
 };
 
 int device_sms();
+// Raises `func`'s dynamic shared-memory limit to `bytes` on the current
+// device, once per (device, kernel): the attribute applies to the device that
+// is current when it is set, so a process that launches on several devices
+// needs it on each.  Returns TL_OK, or TL_ECUDA if the runtime refused.
+int smem_optin(const void* func, int bytes);
 // Adds n to the process-wide launch counter reported by tl_launch_count().
 void count_launches(int n);
 void* workspace(cudaStream_t st, size_t bytes);

@@ -6,14 +6,17 @@
 // rows, so the product is one M x J x n_q matrix product whose row m has its
 // own A and C offsets (from the mapper) and whose k stride is w_q of A: the
 // paper's "slice-times-matrix" reading of ttm (Sec. 5.2), with all slices
-// batched into one launch.  Each CTA computes a 64 x 64 (m, j) tile with a
-// 16-deep k slab staged in shared memory; each thread holds 4 x 4 outputs
-// (ttm_rows_kernel below takes short contractions).
+// batched into one launch.  For FP64 each CTA computes a 64 x 64 (m, j)
+// tile with a 16-deep k slab staged in shared memory, each thread 4 x 4
+// outputs; FP32 runs on the 128 x 128 register-tiled kernel of
+// ttm_sgemm.cu (ttm_rows_kernel below takes short contractions of either).
 // When the (m, j) tiles cannot fill the GPU and n_q is long (a few rows of a
 // matrix-like tensor contracted over most of its elements), the k range is
 // split across CTAs: split s writes its partial M x J block to a workspace
 // and a second kernel adds the splits in order (deterministic) into C.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "device.cuh"
 #include "kernels.h"
@@ -244,9 +247,15 @@ int launch_typed(const TtmPlan& P, const void* A, const void* B, void* C, int ac
         }
         return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
     }
-    int64_t work = a.tiles_m * a.tiles_j * a.splits;
-    int grid = (int)(work < cap ? work : cap);
-    ttm_simt_kernel<T><<<grid, kThreads, 0, st>>>(a);
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the 128 x 128 register-tiled kernel of ttm_sgemm.cu
+        const int rc = launch_ttm_sgemm(P, A, B, C, accumulate, ws, a.splits, a.kchunk, num_sms, st);
+        if (rc != TL_OK) return rc;
+    } else {
+        int64_t work = a.tiles_m * a.tiles_j * a.splits;
+        int grid = (int)(work < cap ? work : cap);
+        ttm_simt_kernel<T><<<grid, kThreads, 0, st>>>(a);
+    }
     if (a.splits > 1) {
         int64_t blocks = (P.M * P.J + kThreads - 1) / kThreads;
         if (blocks > cap) blocks = cap;
@@ -263,10 +272,13 @@ int64_t ttm_simt_splits(const TtmPlan& P, int num_sms, int64_t* kchunk)
         if (kchunk) *kchunk = P.nq;
         return 1;
     }
-    // split k when the tiles cover less than half of two CTAs per SM and each
-    // split still gets at least 16 k slabs; the partials stay below 256 MB
-    const int64_t tiles = ((P.M + BM - 1) / BM) * ((P.J + BJ - 1) / BJ);
-    const int64_t target = (int64_t)num_sms * 4;
+    // split k when the tiles cover less than half of the resident CTAs (one
+    // per SM for the FP32 256-thread tiles, four for the FP64 64 x 64 ones)
+    // and each split still gets at least 16 k slabs of 16; the partials stay
+    // below 256 MB
+    const bool f32 = P.dtype != TL_F64;
+    const int64_t tiles = f32 ? sgemm_tiles(P) : ((P.M + BM - 1) / BM) * ((P.J + BJ - 1) / BJ);
+    const int64_t target = (int64_t)num_sms * (f32 ? 1 : 4);
     int64_t splits = 1;
     if (tiles * 2 < target && P.nq >= 2 * 16 * BK) {
         splits = (target + tiles - 1) / tiles;
@@ -277,6 +289,8 @@ int64_t ttm_simt_splits(const TtmPlan& P, int num_sms, int64_t* kchunk)
         while (splits > 1 && splits * per > (int64_t(256) << 20)) splits /= 2;
     }
     if (splits < 1) splits = 1;
+    // the FP32 kernel counts k within a split in 32-bit arithmetic
+    if (f32 && P.nq >= (int64_t(1) << 30)) splits = std::max<int64_t>(splits, (P.nq >> 29) + 1);
     int64_t kc = (P.nq + splits - 1) / splits;
     kc = (kc + BK - 1) / BK * BK;
     if (kchunk) *kchunk = kc;

@@ -1,8 +1,8 @@
 """Full-size parity in the launch configurations the benchmark times.
 
 - The 512^3 precision workload (mode-3 slices scaled by 10^U(-3,3)): ttm by a
-  512x512 and a truncated 64x512 matrix along every mode in BF16, TF32 and
-  split-BF16x3, and the all-modes Tucker projection to 64^3, checked on
+  512x512 and a truncated 64x512 matrix along every mode in FP32 (SIMT),
+  BF16, TF32 and split-BF16x3, and the all-modes Tucker projection to 64^3, checked on
   sampled outputs against the FP64 oracle.
 - The 4096-operation batch (orders 3-6, extents log-uniform in [4, 64],
   random layouts and modes): one persistent, graph-captured, autotuned launch
@@ -40,7 +40,7 @@ def test_precision_study_all_modes(tl, cuda_dev, precision_case, which):
         C = torch.empty(int(np.prod(nout)), dtype=torch.float32, device=cuda_dev)
         idx = np.stack([g.integers(0, x, size=2000) for x in nout], axis=1)
         ref = oracle.ttm_at(mem, n, w, q, Bm.reshape(-1), 512, 1, idx)
-        for prec in (3, 4, 5):
+        for prec in (2, 3, 4, 5):
             tl.check(tl.tl_ttm(tl.Desc(A, n), Bd, J, 512, 1, q, tl.Desc(C, nout), prec))
             torch.cuda.synchronize()
             got = synth.from_memory(C.cpu().numpy(), nout, (1, 2, 3))[tuple(idx.T)]
