@@ -888,7 +888,7 @@ static int enqueue(Batch* B, cudaStream_t st)
         if (cudaMemsetAsync(B->counter, 0, sizeof(unsigned long long), st) != cudaSuccess) return TL_ECUDA;
         batch_kernel<<<grid_size(), kThreads, 0, st>>>(B->dev_ops, (int)B->host.size(),
                                                        B->total_units, B->counter);
-        if (cudaPeekAtLastError() != cudaSuccess) return TL_ECUDA;
+        if (cudaGetLastError() != cudaSuccess) return TL_ECUDA;
     }
     return TL_OK;
 }
@@ -994,12 +994,21 @@ int batch_describe(const Batch* B, char* buf, size_t len)
 {
     if (!B || !buf || !len) return TL_EINVAL;
     int hist[16] = {0};
-    for (const BOp& b : B->host) hist[b.variant & 15]++;
+    // operations whose recorded unit does not fit them (a cached choice that
+    // escaped sanitize); the device-side checks are the second guard
+    int unfit = 0;
+    for (const BOp& b : B->host) {
+        hist[b.variant & 15]++;
+        const Candidate c{b.variant, b.unit};
+        const Candidate s = sanitize(c, b);
+        if (s.variant != c.variant || s.unit != c.unit) ++unfit;
+    }
     std::snprintf(buf, len,
                   "{\"ops\":%zu,\"direct\":%d,\"units\":%lld,\"grid\":%d,\"bytes\":%zu,"
+                  "\"unfit\":%d,"
                   "\"variants\":{\"ttv_col\":%d,\"ttv_row4\":%d,\"ttv_row8\":%d,\"ttv_row32\":%d,"
                   "\"ttm32\":%d,\"ttm64\":%d,\"ew\":%d,\"ttm_small\":%d,\"ttv_vec\":%d}}",
-                  B->host.size(), B->direct, (long long)B->total_units, grid_size(), B->bytes,
+                  B->host.size(), B->direct, (long long)B->total_units, grid_size(), B->bytes, unfit,
                   hist[0], hist[1], hist[2], hist[3], hist[4], hist[5], hist[6], hist[7], hist[8]);
     return TL_OK;
 }
@@ -1079,7 +1088,7 @@ int slot_launch(Slot* s, const tl_op* const* ops, size_t n, cudaStream_t st)
         cudaMemsetAsync(s->counter, 0, sizeof(unsigned long long), st) != cudaSuccess)
         return TL_ECUDA;
     batch_kernel<<<grid_size(), kThreads, 0, st>>>(s->dev, (int)m, units, s->counter);
-    if (cudaPeekAtLastError() != cudaSuccess) return TL_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) return TL_ECUDA;
     count_launches(1);
     return TL_OK;
 }

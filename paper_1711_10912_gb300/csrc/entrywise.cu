@@ -363,7 +363,7 @@ int launch_typed(const EwPlan& P, const void* A, const void* B, double alpha, vo
     } else {
         ew_generic_kernel<T><<<grid_for(P.N, num_sms), kThreads, 0, st>>>(a);
     }
-    return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
 }
 
 }  // namespace

@@ -29,6 +29,7 @@
 #include <cstdint>
 
 #include "kernels.h"
+#include "runtime.h"
 #include "pipeline.cuh"
 #include "plan.h"
 
@@ -391,17 +392,16 @@ int launch_ew_tma(const EwPlan& P, const void* A, const void* B, double alpha, v
     a.nstages = a.nin == 2 ? 2 : 3;
     a.off_bar = a.nstages * a.stage_bytes;
     const uint32_t smem = a.off_bar + 16 * a.nstages + 1024;
-    static std::atomic<bool> attr_set{false};
-    if (!attr_set.load()) {
-        const int lim = 227 * 1024;
-        cudaFuncSetAttribute(ew_tma_kernel<TL_ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(ew_tma_kernel<TL_SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(ew_tma_kernel<TL_MUL>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(ew_tma_kernel<TL_DIV>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(ew_tma_kernel<TL_COPY>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(ew_tma_kernel<TL_SCALE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        attr_set.store(true);
+    int rc;
+    switch (a.op) {
+    case TL_ADD: rc = smem_optin(reinterpret_cast<const void*>(ew_tma_kernel<TL_ADD>), (int)smem); break;
+    case TL_SUB: rc = smem_optin(reinterpret_cast<const void*>(ew_tma_kernel<TL_SUB>), (int)smem); break;
+    case TL_MUL: rc = smem_optin(reinterpret_cast<const void*>(ew_tma_kernel<TL_MUL>), (int)smem); break;
+    case TL_DIV: rc = smem_optin(reinterpret_cast<const void*>(ew_tma_kernel<TL_DIV>), (int)smem); break;
+    case TL_COPY: rc = smem_optin(reinterpret_cast<const void*>(ew_tma_kernel<TL_COPY>), (int)smem); break;
+    default: rc = smem_optin(reinterpret_cast<const void*>(ew_tma_kernel<TL_SCALE>), (int)smem); break;
     }
+    if (rc != TL_OK) return TL_ECUDA;
     const int64_t cap = (int64_t)num_sms * ctas;
     const int grid = (int)(a.ntiles < cap ? a.ntiles : cap);
     switch (a.op) {
@@ -412,7 +412,7 @@ int launch_ew_tma(const EwPlan& P, const void* A, const void* B, double alpha, v
     case TL_COPY: ew_tma_kernel<TL_COPY><<<grid, kThreadsTma, smem, st>>>(maps[0], maps[1], a, nds[0], nds[1]); break;
     default: ew_tma_kernel<TL_SCALE><<<grid, kThreadsTma, smem, st>>>(maps[0], maps[1], a, nds[0], nds[1]); break;
     }
-    return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
 }
 
 int ew_status(bool clear)

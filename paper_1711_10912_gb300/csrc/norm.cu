@@ -138,7 +138,7 @@ int launch_norm(const Space& sp, int dx, const void* X, int dr, const void* R, d
         launch_pass1<float, float, true>(a, nblocks, partials, st);
     }
     norm_final_kernel<<<1, kThreads, 0, st>>>(partials, nblocks, R ? 1 : 0, result);
-    return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
 }
 
 }  // namespace tl

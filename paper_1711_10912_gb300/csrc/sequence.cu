@@ -286,7 +286,7 @@ int tl_hopm(const tl_tensor* A_, void* const* u, double* lambda, uint32_t K, voi
                 normalize_kernel<float><<<grid, kThreads, 0, st>>>(
                     static_cast<const float*>(tmp), static_cast<float*>(u[r - 1]), nr, nrm,
                     lambda + (r - 1));
-            if (cudaPeekAtLastError() != cudaSuccess) return TL_ECUDA;
+            if (cudaGetLastError() != cudaSuccess) return TL_ECUDA;
             count_launches(1);
         }
     }

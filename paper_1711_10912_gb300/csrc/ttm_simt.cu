@@ -245,7 +245,7 @@ int launch_typed(const TtmPlan& P, const void* A, const void* B, void* C, int ac
         case 2: ttm_rows_kernel<T, 2><<<(int)blocks, kThreads, smem, st>>>(a); break;
         default: ttm_rows_kernel<T, 1><<<(int)blocks, kThreads, smem, st>>>(a); break;
         }
-        return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
+        return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
     }
     if constexpr (sizeof(T) == 4) {
         // FP32: the 128 x 128 register-tiled kernel of ttm_sgemm.cu
@@ -261,7 +261,7 @@ int launch_typed(const TtmPlan& P, const void* A, const void* B, void* C, int ac
         if (blocks > cap) blocks = cap;
         ttm_splitk_reduce<T><<<(int)blocks, kThreads, 0, st>>>(a);
     }
-    return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
 }
 
 }  // namespace

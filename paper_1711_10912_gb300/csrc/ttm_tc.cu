@@ -192,10 +192,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// FP32 -> TF32 rounded to nearest, ties to even (the same rule as the BF16
+// conversions), so TF32 results do not drift away from zero on ties
 __device__ __forceinline__ uint32_t to_tf32(float x)
 {
     uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    asm("cvt.rn.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return r;
 }
 
@@ -947,14 +949,11 @@ int launch_prec(const TtmPlan& P, const void* A, const void* B, void* C, int acc
                                                   P.ldb_col, (int)P.J, L.Jp, P.nq, L.nks, img,
                                                   L.opb_part);
     }
-    static std::once_flag once[6];
-    std::call_once(once[PREC], [&] {
-        cudaFuncSetAttribute(ttm_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             227 * 1024);
-    });
+    if (smem_optin(reinterpret_cast<const void*>(ttm_tc_kernel<PREC>), (int)L.smem) != TL_OK)
+        return TL_ECUDA;
     int grid = (int)(a.ntiles < sms ? a.ntiles : sms);
     ttm_tc_kernel<PREC><<<grid, kThreads, L.smem, st>>>(map, cmap, a);
-    return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
 }
 
 }  // namespace
@@ -992,7 +991,7 @@ int selftest_wait_timeout(double limit_us, cudaStream_t st)
     if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0) khz = 2000000;
     const long long cycles = (long long)(limit_us * 1e-3 * khz);
     selftest_wait_kernel<<<1, 32, 0, st>>>(cycles);
-    return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
 }
 
 int ttm_tc_status(bool clear)

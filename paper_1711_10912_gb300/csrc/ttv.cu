@@ -21,6 +21,7 @@
 #include "device.cuh"
 #include "kernels.h"
 #include "pipeline.cuh"
+#include "runtime.h"
 
 namespace tl {
 
@@ -367,16 +368,12 @@ int launch_typed(const TtvPlan& P, const void* A, const void* b, void* C, void* 
         r.off_b = r.nstages * r.stage_bytes;
         r.off_bar = r.off_b + (uint32_t)((row_bytes + 127) / 128 * 128);
         const uint32_t smem = r.off_bar + 16 * r.nstages;
-        static bool attr_set[2] = {false, false};
-        if (!attr_set[sizeof(T) == 8]) {
-            cudaFuncSetAttribute(ttv_row_staged_kernel<T>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-            attr_set[sizeof(T) == 8] = true;
-        }
+        if (smem_optin(reinterpret_cast<const void*>(ttv_row_staged_kernel<T>), (int)smem) != TL_OK)
+            return TL_ECUDA;
         const int64_t nchunks = (P.nout + r.rows_per_stage - 1) / r.rows_per_stage;
         const int grid = (int)std::min<int64_t>(nchunks, (int64_t)num_sms * 3);
         ttv_row_staged_kernel<T><<<grid, kStageThreads, smem, st>>>(r);
-        return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
+        return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
     }
     if (P.kernel == K_TTV_ROW) {
         int64_t threads = (P.nout + 3) / 4 * P.lanes;
@@ -407,7 +404,7 @@ int launch_typed(const TtvPlan& P, const void* A, const void* b, void* C, void* 
     if (P.splits > 1) {
         ttv_splitk_reduce<T><<<grid_for(P.nout, num_sms), kThreads, 0, st>>>(a);
     }
-    return cudaPeekAtLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
 }
 
 }  // namespace
@@ -449,8 +446,6 @@ int launch_ttv(const TtvPlan& P, const void* A, const void* b, void* C, void* ws
 
 #include <atomic>
 #include <mutex>
-
-#include "runtime.h"
 
 static __device__ __align__(256) unsigned char g_ttv_noalloc_scratch[TL_TTV_NOALLOC_SCRATCH_BYTES];
 

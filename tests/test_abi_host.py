@@ -36,6 +36,21 @@ def test_library_exports_every_declared_symbol(tl):
         assert hasattr(tl._lib, name), f"{name} not exported by libtlgb.so"
 
 
+def test_binding_constants_match_the_header(tl):
+    # the binding restates a few of tlgb.h's macros; they must not drift apart
+    with open(os.path.join(ROOT, "include", "tlgb.h")) as fh:
+        src = fh.read()
+    m = re.search(r"#define\s+TL_TTV_NOALLOC_SCRATCH_BYTES\s+\((\d+)u\s*<<\s*(\d+)\)", src)
+    assert m, "TL_TTV_NOALLOC_SCRATCH_BYTES not found in tlgb.h"
+    assert tl.TL_TTV_NOALLOC_SCRATCH_BYTES == int(m.group(1)) << int(m.group(2))
+    for name in ("TL_OK", "TL_EINVAL", "TL_EUNSUPPORTED", "TL_ENOMEM", "TL_ECUDA", "TL_ETIMEOUT",
+                 "TL_P_F64", "TL_P_F32", "TL_P_TF32", "TL_P_BF16", "TL_P_BF16X3",
+                 "TL_OP_TTV", "TL_OP_TTM", "TL_OP_ENTRYWISE"):
+        m = re.search(r"#define\s+%s\s+(-?\d+)" % name, src)
+        if m and hasattr(tl, name):
+            assert getattr(tl, name) == int(m.group(1)), name
+
+
 def test_strerror_and_version(tl):
     assert tl.tl_version() >= 100
     assert tl.tl_strerror(tl.TL_EINVAL) == "invalid argument"

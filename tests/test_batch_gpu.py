@@ -239,6 +239,12 @@ dev = torch.device("cuda", 0)
 s = OpSet(tl, dev, 160, 7700, "f32")
 rc, b = tl.tl_batch_create(s.ops, tl.TL_BATCH_TUNE)
 tl.check(rc)
+rc, desc = tl.tl_batch_describe(b)
+tl.check(rc)
+print(desc, flush=True)
+# the host check comes first: a unit that does not fit its operation is never run
+if json.loads(desc)["unfit"] != 0:
+    sys.exit(3)
 tl.check(tl.tl_batch_run(b))
 worst = s.check()
 tl.tl_batch_destroy(b)
@@ -268,5 +274,9 @@ def test_batch_poisoned_tune_cache_is_ignored(tl, cuda_dev, tmp_path):
     cache.write_text("\n".join(poisoned) + "\n")
     second = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
                             timeout=600)
+    out = second.stdout.strip().splitlines()
+    # the host-side description was printed before the run and shows every
+    # poisoned choice replaced
+    assert out and json.loads(out[0])["unfit"] == 0, second.stdout[-2000:]
     assert second.returncode == 0, second.stderr[-2000:]
-    assert json.loads(second.stdout.strip().splitlines()[-1])["worst"] <= TOL["f32"]
+    assert json.loads(out[-1])["worst"] <= TOL["f32"]

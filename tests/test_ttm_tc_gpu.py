@@ -176,3 +176,40 @@ def test_tc_store_paths_bit_exact(tl, cuda_dev, prec, case):
     np.testing.assert_array_equal(out[off:off + NC], ref)
     assert np.all(out[:off] == -7.0) and np.all(out[off + NC:] == -7.0)
     assert tl.tl_device_status() == tl.TL_OK
+
+
+def _round_even(x, drop):
+    """FP32 values rounded to nearest, ties to even, keeping 23 - drop
+    mantissa bits (drop = 13: TF32, 16: BF16); finite inputs."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (b >> drop) & 1
+    b = (b + (1 << (drop - 1)) - 1 + lsb) & ~np.uint64((1 << drop) - 1)
+    return b.astype(np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("prec,drop", [("tf32", 13), ("bf16", 16)])
+def test_tc_conversion_rounds_ties_to_even(tl, cuda_dev, prec, drop):
+    # A holds values exactly halfway between two representable TF32 / BF16
+    # values (and their neighbours); with B = I each output is one converted
+    # element times 1, so C shows the rounding rule: ties go to the even
+    # neighbour (1 + 2^-11 -> 1 in TF32, where ties away from zero would give
+    # 1 + 2^-10), never away from zero
+    n, q, J = (256, 32), 2, 32
+    half = np.float32(2.0 ** (-(24 - drop)))          # half an ulp at 1.0
+    base = np.array([1.0, 1.0 + 2 * half, -1.0, -(1.0 + 2 * half), 1.5, 3.0], np.float32)
+    g = synth.rng(6900)
+    vals = np.concatenate([base + half, base - half, base + half / 2, base + 3 * half,
+                           base])
+    X = g.choice(vals, size=n).astype(np.float32) * np.float32(2.0) ** g.integers(-4, 5, size=n)
+    X = X.astype(np.float32)
+    A = put(X, (1, 2), cuda_dev, "f32")
+    C = torch.empty(n[0] * J, dtype=torch.float32, device=cuda_dev)
+    assert plan_kernel(tl, A, n, (1, 2), q, J, C, PREC[prec])["kernel"] == "ttm_tc"
+    got, _ = ttm_case(tl, cuda_dev, X, q, np.eye(J), (1, 2), (1, 2), "f32",
+                      precision=PREC[prec])
+    want = _round_even(X, drop)
+    np.testing.assert_array_equal(got, want)
+    # the fixture really holds ties: rounding them away from zero differs
+    b = np.ascontiguousarray(X).view(np.uint32).astype(np.uint64)
+    away = ((b + (1 << (drop - 1))) & ~np.uint64((1 << drop) - 1)).astype(np.uint32)
+    assert np.count_nonzero(away.view(np.float32) != want) > 100
