@@ -58,7 +58,7 @@ def parse_args():
                     help="TL_P_* for the ttm calls (2 = FP32 SIMT, 5 = split-BF16x3)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=1 << 19,
+    ap.add_argument("--cpu-sample", type=int, default=1 << 18,
                     help="outputs per ttv/ttm op in the CPU-oracle sample")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -284,10 +284,47 @@ def kernel_of(tl, wl, c):
 
 # ------------------------------------------------------------ CPU oracle ---
 
-def cpu_oracle_sample(case, memF64, memL64, edge, per_op, g):
+def host_cpu():
+    """Core count and CPU model of this host (recorded beside every CPU number)."""
+    import platform
+    import subprocess
+    usable = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip().lower() == "model name":
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for ln in fh:
+                    key = ln.split(":")[0].strip().lower()
+                    if key in ("model name", "cpu part"):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"host_cores": os.cpu_count(), "usable_cores": usable,
+            "cpu_model": model or platform.processor() or "unknown",
+            "arch": platform.machine()}
+
+
+def _chunks(arr, k):
+    k = max(1, min(k, len(arr)))
+    return [c for c in np.array_split(arr, k) if len(c)]
+
+
+def cpu_oracle_sample(case, memF64, memL64, edge, per_op, g, threads=1):
     """Times the FP64 oracle on a bounded sample of one step: per_op sampled
     outputs of every ttv and ttm call and a per_op*edge-element block of the
-    entrywise add.  Returns (seconds, algorithmic bytes represented)."""
+    entrywise add.  With threads > 1 each call's sample is split across that
+    many threads (the oracle's C functions run without the interpreter lock).
+    Returns (seconds, algorithmic bytes represented)."""
+    from concurrent.futures import ThreadPoolExecutor
     import oracle
     import synth
     p = 4
@@ -296,48 +333,131 @@ def cpu_oracle_sample(case, memF64, memL64, edge, per_op, g):
     sec, byts = 0.0, 0.0
     b_ttv = (N + N // edge + edge) * 4
     b_ttm = (2 * N + edge * edge) * 4
+    ex = ThreadPoolExecutor(max_workers=threads) if threads > 1 else None
+
+    def run(fn, parts):
+        if ex is None:
+            for a in parts:
+                fn(a)
+        else:
+            list(ex.map(fn, parts))
+
     for pi, mem in ((synth.first_order(p), memF64), (synth.last_order(p), memL64)):
         w = oracle.strides(n, pi)
         for q in range(1, p + 1):
             idx = np.stack([g.integers(0, edge, size=per_op) for _ in range(p - 1)], axis=1)
             bq = case.vectors[q - 1].astype(np.float64)
+            parts = _chunks(idx, threads)
             t0 = time.perf_counter()
-            oracle.ttv_at(mem, n, w, q, bq, idx)
+            run(lambda ix: oracle.ttv_at(mem, n, w, q, bq, ix), parts)
             sec += time.perf_counter() - t0
             byts += b_ttv * per_op / (N // edge)
         for q in range(1, p + 1):
             idx = np.stack([g.integers(0, edge, size=per_op) for _ in range(p)], axis=1)
             Bq = case.matrices[q - 1].astype(np.float64).reshape(-1)
+            parts = _chunks(idx, threads)
             t0 = time.perf_counter()
-            oracle.ttm_at(mem, n, w, q, Bq, edge, 1, idx)
+            run(lambda ix: oracle.ttm_at(mem, n, w, q, Bq, edge, 1, ix), parts)
             sec += time.perf_counter() - t0
             byts += b_ttm * per_op / N
     # entrywise add over the first `s` slices of mode 4 of both layouts
     s = max(1, min(edge, per_op * edge // (edge ** 3)))
-    nsub = (edge, edge, edge, s)
     wF = oracle.strides(n, synth.first_order(p))
     wL = oracle.strides(n, synth.last_order(p))
+    bounds = np.linspace(0, s, min(threads, s) + 1).astype(int)
+    blocks = [(int(a), int(b)) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
     t0 = time.perf_counter()
-    oracle.entrywise(oracle.OP_ADD, nsub, memF64, wF, memL64, wL)
+    run(lambda ab: oracle.entrywise(oracle.OP_ADD, (edge, edge, edge, ab[1] - ab[0]), memF64, wF,
+                                    memL64, wL, offA=ab[0] * wF[3], offB=ab[0] * wL[3]), blocks)
     sec += time.perf_counter() - t0
     byts += 3 * 4 * edge ** 3 * s
+    if ex is not None:
+        ex.shutdown()
     return sec, byts
 
 
-def cpu_baseline(case, edge, per_op):
+def cpu_method_sample(case, memF, memL, edge, slices, nthreads):
+    """Times the paper's plain recursive method (cpu_method, FP32, OpenMP
+    over the outermost recursion level) on the first `slices` indices of the
+    outermost free mode of every ttv and ttm call and of mode 4 of the add.
+    Returns (seconds, algorithmic bytes represented, threads used)."""
+    import cpu_method
+    import oracle
     import synth
+    p = 4
+    n = (edge,) * p
+    N = edge ** p
+    used = cpu_method.threads(nthreads)
+    out = np.empty(N, np.float32)
+    sec, byts = 0.0, 0.0
+    b_ttv = (N + N // edge + edge) * 4
+    b_ttm = (2 * N + edge * edge) * 4
+    frac = slices / edge
+    for pi, mem in ((synth.first_order(p), memF), (synth.last_order(p), memL)):
+        w = oracle.strides(n, pi)
+        for q in range(1, p + 1):
+            nout = tuple(x for r, x in enumerate(n) if r != q - 1)
+            pic = tuple(sorted(r for r in pi if r != q).index(r) + 1 for r in pi if r != q)
+            wC = oracle.strides(nout, pic)
+            wC_by_A = [0] * p
+            for r, c in zip([r for r in range(p) if r != q - 1], range(p - 1)):
+                wC_by_A[r] = wC[c]
+            b = np.ascontiguousarray(case.vectors[q - 1], dtype=np.float32)
+            t0 = time.perf_counter()
+            cpu_method.ttv(mem, n, w, q, b, out, wC_by_A, count=slices, nthreads=nthreads)
+            sec += time.perf_counter() - t0
+            byts += b_ttv * frac
+        for q in range(1, p + 1):
+            Bq = np.ascontiguousarray(case.matrices[q - 1], dtype=np.float32).reshape(-1)
+            t0 = time.perf_counter()
+            cpu_method.ttm(mem, n, w, q, Bq, edge, edge, 1, out, w, count=slices,
+                           nthreads=nthreads)
+            sec += time.perf_counter() - t0
+            byts += b_ttm * frac
+    wF = oracle.strides(n, synth.first_order(p))
+    wL = oracle.strides(n, synth.last_order(p))
+    t0 = time.perf_counter()
+    cpu_method.transform(0, memF, wF, memL, wL, out, wF, n, count=slices, nthreads=nthreads)
+    sec += time.perf_counter() - t0
+    byts += 3 * 4 * N * frac
+    return sec, byts, used
+
+
+def cpu_baseline(case, edge, per_op):
+    """The CPU legs beside the GPU numbers: the FP64 oracle on one core and on
+    every usable core (the same sample), and the paper's plain recursive
+    method (FP32) on every usable core, all on this host."""
+    import synth
+    host = host_cpu()
+    cores = host["usable_cores"]
     memF64 = case.mem_first.astype(np.float64)
     X = synth.from_memory(case.mem_first, (edge,) * 4, synth.first_order(4))
-    memL64 = synth.to_memory(X, synth.last_order(4)).astype(np.float64)
+    memL = synth.to_memory(X, synth.last_order(4)).astype(np.float32)
     del X
-    g = synth.rng(99)
-    sec, byts = cpu_oracle_sample(case, memF64, memL64, edge, per_op, g)
-    return {"value": byts / sec / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "seconds": round(sec, 3),
-            "sample": f"{per_op} sampled outputs of each of the 8 ttv and 8 ttm calls, and a "
-                      f"{edge}^3 x {max(1, min(edge, per_op * edge // edge ** 3))} block of the "
-                      "entrywise add, FP64 oracle single-threaded; bytes scaled by the sampled "
-                      "fraction of each call"}
+    memL64 = memL.astype(np.float64)
+    s1, b1 = cpu_oracle_sample(case, memF64, memL64, edge, per_op, synth.rng(99), threads=1)
+    sn, bn = cpu_oracle_sample(case, memF64, memL64, edge, per_op, synth.rng(99), threads=cores)
+    del memF64, memL64
+    slices = max(1, min(edge, cores))
+    sm, bm, used = cpu_method_sample(case, np.ascontiguousarray(case.mem_first, np.float32), memL,
+                                     edge, slices, cores)
+    blk = max(1, min(edge, per_op * edge // edge ** 3))
+    sample = (f"{per_op} sampled outputs of each of the 8 ttv and 8 ttm calls and a {edge}^3 x "
+              f"{blk} block of the entrywise add, FP64 oracle; bytes scaled by the sampled "
+              "fraction of each call")
+    return {"value": bn / sn / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "seconds": round(sn, 3), "sample": sample, **host, "cores_used": cores,
+            "oracle_1core": {"value": b1 / s1 / 1e9, "unit": "GB/s", "cores": 1,
+                             "seconds": round(s1, 3)},
+            "oracle_all_cores": {"value": bn / sn / 1e9, "unit": "GB/s", "cores": cores,
+                                 "seconds": round(sn, 3),
+                                 "speedup_over_1core": round(s1 / sn, 2)},
+            "plain_method": {"value": bm / sm / 1e9, "unit": "GB/s", "cores": used,
+                             "seconds": round(sm, 3), "dtype": "f32",
+                             "kind": "the paper's recursive ttv / ttm / transform (Secs. 5.1-5.2) "
+                                     "in plain C++, OpenMP over the outermost recursion level",
+                             "sample": f"the first {slices} of {edge} indices of the outermost "
+                                       "free mode of each of the 17 calls"}}
 
 
 # ------------------------------------------------------------ main arms ---
@@ -355,13 +475,15 @@ def reference_arm(args):
     X = synth.from_memory(case.mem_first, (edge,) * 4, synth.first_order(4))
     memL64 = synth.to_memory(X, synth.last_order(4)).astype(np.float64)
     del X
+    host = host_cpu()
+    cores = host["usable_cores"]
     per_op = 1 << 15
     g = synth.rng(7)
     for _ in range(args.warmup):
-        cpu_oracle_sample(case, memF64, memL64, edge, per_op, g)
+        cpu_oracle_sample(case, memF64, memL64, edge, per_op, g, threads=cores)
     tot_s, tot_b = 0.0, 0.0
     for _ in range(args.steps):
-        s, b = cpu_oracle_sample(case, memF64, memL64, edge, per_op, g)
+        s, b = cpu_oracle_sample(case, memF64, memL64, edge, per_op, g, threads=cores)
         tot_s += s
         tot_b += b
     v = tot_b / tot_s / 1e9
@@ -371,10 +493,12 @@ def reference_arm(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": WORKLOAD, "edge": edge, "l2": "inputs larger than L2",
-                       "parallelism": "single process, host CPU"},
-            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                       "parallelism": "single process, every usable host core"},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             **host,
                              "sample": f"{per_op} sampled outputs per ttv/ttm call and a "
-                                       "slice block of the add per step"},
+                                       "slice block of the add per step, split across "
+                                       f"{cores} threads"},
             "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
