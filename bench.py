@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=1 << 18,
                     help="outputs per ttv/ttm op in the CPU-oracle sample")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the FP64 calls timed against the measured DFMA rate")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-next", action="store_true",
@@ -617,7 +619,11 @@ def main():
 
     extras = {}
     step_bytes, step_flops = wl.step_bytes, wl.step_flops
+    fma = None
     if world == 1:
+        fma = measure_fma_peaks(tl, torch, dev, sh, gpu_id(torch, dev))
+        extras["peaks_measured"] = fma
+        extras["ttm_f32_default"] = measure_ttm_f32_default(tl, torch, wl, sh, peaks, fma)
         del wl
         torch.cuda.empty_cache()
         if not args.no_batch:
@@ -629,12 +635,18 @@ def main():
             torch.cuda.empty_cache()
         if not args.no_precision:
             extras["precision"] = measure_precision(tl, torch, dev, sh)
+            for c in extras["precision"]["cases"]:
+                if c["precision"] == "f32" and fma:
+                    c["frac_fma"] = round(c["TFLOP/s"] / fma["fp32_tflops"], 3)
             torch.cuda.empty_cache()
         if not args.no_next:
             extras["next"] = measure_next(tl, torch, dev, sh, edge, peaks)
             torch.cuda.empty_cache()
         if not args.no_small:
-            extras["small"] = measure_small(tl, torch, dev, sh, rank == 0)
+            extras["small"] = measure_small(tl, torch, dev, sh, rank == 0, fma=fma, peaks=peaks)
+            torch.cuda.empty_cache()
+        if not args.no_fp64:
+            extras["fp64"] = measure_fp64(tl, torch, dev, sh, fma, peaks)
             torch.cuda.empty_cache()
 
     cpu = None
@@ -864,6 +876,133 @@ def measure_serve(tl, torch, dev, sh, nreq, rates, pool=192, budget=40_000_000_0
     return out
 
 
+def measure_ttm_f32_default(tl, torch, wl, sh, peaks, fma, reps=3):
+    """ttm of the 128^4 tensors in the precision a caller gets by default for
+    FP32 data (FP32 FMAs on the SIMT pipes), along every mode of both
+    layouts: time and fractions of HBM and of the measured FP32 FMA rate."""
+    edge = wl.n[0]
+    out = {"precision": "f32 (TL_P_DEFAULT)", "fma_tflops": fma["fp32_tflops"],
+           "hbm_gbs": peaks["hbm_gbs"], "calls": {}}
+    byts, flops = wl.bytes["ttm"], wl.flops["ttm"]
+    for c in wl.calls:
+        if c[0] != "ttm":
+            continue
+        q = c[2]
+        fn = lambda: tl.check(tl.tl_ttm(c[3], wl.B[q - 1], edge, edge, 1, q, c[4],
+                                        tl.TL_P_DEFAULT, 0, sh))
+        ms = _time_ms(torch, fn, reps)
+        tf = flops / (ms / 1e3) / 1e12
+        gbs = byts / (ms / 1e3) / 1e9
+        out["calls"][f"{c[1]}_q{q}"] = {"ms": round(ms, 4), "TFLOP/s": round(tf, 2),
+                                        "GB/s": round(gbs, 1),
+                                        "frac_fma": round(tf / fma["fp32_tflops"], 3),
+                                        "frac_hbm": round(gbs / peaks["hbm_gbs"], 3)}
+    return out
+
+
+# ------------------------------------------------------- measured peaks ---
+
+def measure_fma_peaks(tl, torch, dev, sh, gpu, target_ms=40.0):
+    """FP32 FMA and FP64 DFMA rates of this GPU, measured with the library's
+    probe kernel (every SM busy with independent fused multiply-adds): the
+    best of 3 launches of about target_ms each, with the SM clock sampled
+    meanwhile, and the FMA lanes per SM and clock that the rate implies."""
+    sink = torch.zeros(1, dtype=torch.float64, device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(dtype, iters):
+        rc, fl = tl.tl_fma_peak_probe(dtype, iters, sink, sh)
+        tl.check(rc, "tl_fma_peak_probe")
+        e0.record()
+        rc, fl = tl.tl_fma_peak_probe(dtype, iters, sink, sh)
+        e1.record()
+        torch.cuda.synchronize()
+        return fl, e0.elapsed_time(e1)
+
+    out = {"kernel": "fma_probe_kernel", "sms": sms}
+    cs = ClockSampler(gpu)
+    cs.start()
+    for name, dtype in (("fp32", tl.TL_F32), ("fp64", tl.TL_F64)):
+        fl, ms = timed(dtype, 1 << 12)
+        iters = max(16, int((1 << 12) * target_ms / max(ms, 1e-3)) // 16 * 16)
+        best = 0.0
+        for _ in range(3):
+            fl, ms = timed(dtype, iters)
+            best = max(best, fl / (ms / 1e3))
+        out[f"{name}_tflops"] = round(best / 1e12, 3)
+    clk = cs.stop()
+    out["clocks"] = clk
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz")
+    if mhz:
+        for name in ("fp32", "fp64"):
+            out[f"{name}_fma_per_sm_per_clock"] = round(
+                out[f"{name}_tflops"] * 1e12 / 2 / (sms * mhz * 1e6), 2)
+    return out
+
+
+def attainable(flops, byts, peak_tflops, hbm_gbs):
+    """min(compute peak, arithmetic intensity x HBM bandwidth) in TFLOP/s."""
+    return min(peak_tflops, flops / byts * hbm_gbs / 1e3)
+
+
+def measure_fp64(tl, torch, dev, sh, fma, peaks, reps=5):
+    """FP64 calls against min(measured DFMA rate, AI x HBM): ttv and ttm (J =
+    64) of a 256^3 FP64 tensor along modes 1 and 3, and the largest FP64 ttm
+    of the serving pool."""
+    import synth
+    pk64, hbm = fma["fp64_tflops"], peaks["hbm_gbs"]
+    out = {"dfma_tflops": pk64, "hbm_gbs": hbm, "calls": {}}
+
+    def record(name, fn, flops, byts):
+        ms = _time_ms(torch, fn, reps)
+        tf = flops / (ms / 1e3) / 1e12
+        att = attainable(flops, byts, pk64, hbm)
+        out["calls"][name] = {"ms": round(ms, 4), "TFLOP/s": round(tf, 3),
+                              "GB/s": round(byts / (ms / 1e3) / 1e9, 1),
+                              "AI_flop_per_byte": round(flops / byts, 3),
+                              "attainable_TFLOP/s": round(att, 3),
+                              "bound": "dfma" if att >= pk64 else "hbm",
+                              "frac": round(tf / att, 3)}
+
+    e = 256
+    n = (e, e, e)
+    N = e ** 3
+    A = synth.device_normal(torch, N, 61_000, torch.float64, dev)
+    b = synth.device_normal(torch, e, 61_001, torch.float64, dev)
+    B = synth.device_normal(torch, 64 * e, 61_002, torch.float64, dev)
+    Cv = torch.empty(N // e, dtype=torch.float64, device=dev)
+    Cm = torch.empty(N // e * 64, dtype=torch.float64, device=dev)
+    for q in (1, 3):
+        nv = tuple(x for r, x in enumerate(n) if r != q - 1)
+        nm = tuple(64 if r == q - 1 else x for r, x in enumerate(n))
+        DA, DV, DM = tl.Desc(A, n), tl.Desc(Cv, nv), tl.Desc(Cm, nm)
+        record(f"ttv_256^3_q{q}", lambda: tl.check(tl.tl_ttv(DA, b, 1, q, DV, 0, sh)),
+               2 * N, (N + N // e + e) * 8)
+        record(f"ttm_256^3_x64_q{q}",
+               lambda: tl.check(tl.tl_ttm(DA, B, 64, e, 1, q, DM, tl.TL_P_F64, 0, sh)),
+               2 * N * 64, (N + N // e * 64 + 64 * e) * 8)
+    del A, Cv, Cm
+    # the serving pool's largest FP64 ttm (by flops)
+    reqs = synth.serving_stream(192, 1.0, seed=synth.BASE_SEED + 5)
+    big = max((r for r in reqs if r.op == "ttm" and r.dtype == "f64"),
+              key=lambda r: int(np.prod(r.n)) * r.J, default=None)
+    if big is not None:
+        n, q, J = big.n, big.q, big.J
+        N = int(np.prod(n))
+        A = synth.device_normal(torch, N, 61_010, torch.float64, dev)
+        B = synth.device_normal(torch, J * n[q - 1], 61_011, torch.float64, dev)
+        C = torch.empty(N // n[q - 1] * J, dtype=torch.float64, device=dev)
+        nout = tuple(J if r == q - 1 else x for r, x in enumerate(n))
+        DA, DC = tl.Desc(A, n, big.pi), tl.Desc(C, nout, big.pi)
+        record("serving_pool_largest_fp64_ttm",
+               lambda: tl.check(tl.tl_ttm(DA, B, J, n[q - 1], 1, q, DC, tl.TL_P_F64, 0, sh)),
+               2 * N * J, (N + N // n[q - 1] * J + J * n[q - 1]) * 8)
+        out["calls"]["serving_pool_largest_fp64_ttm"]["shape"] = {
+            "n": list(n), "pi": list(big.pi), "q": q, "J": J}
+    return out
+
+
 # ------------------------------------------------------------ precision ---
 
 def measure_precision(tl, torch, dev, sh, edge=512, rank=64, samples=3000):
@@ -1048,7 +1187,7 @@ def measure_next(tl, torch, dev, sh, edge, peaks):
     return out
 
 
-def measure_small(tl, torch, dev, sh, with_oracle, reps=200):
+def measure_small(tl, torch, dev, sh, with_oracle, reps=200, fma=None, peaks=None):
     """The small plain-method case: order-3 FP64 64^3 (first-order), ttv along
     mode 2, ttm along mode 1 with a 32 x 64 matrix, add with a last-order copy.
     Everything is L2-resident, so the numbers are latencies: device time per
@@ -1078,6 +1217,7 @@ def measure_small(tl, torch, dev, sh, with_oracle, reps=200):
                          (N + J * n[1] * n[2] + J * n[0]) * 8),
         "add_first+last": (lambda st: tl.tl_entrywise(tl.TL_ADD, DA, DL, 1.0, DCe, st), 3 * N * 8),
     }
+    flops = {"ttv_q2": 2 * N, "ttm_q1_32x64": 2 * N * J, "add_first+last": N}
     w = oracle.strides(n, piF)
     oracle_calls = {
         "ttv_q2": lambda: oracle.ttv(memF, n, w, 2, case.b),
@@ -1121,6 +1261,14 @@ def measure_small(tl, torch, dev, sh, with_oracle, reps=200):
                "host_enqueue_us_per_call": round(t_enq * 1e6, 2),
                "host_us_per_call_synchronous": round(sync_us, 2),
                "kernels_per_call": launches, "GB/s_device": round(byts / (dev_us / 1e6) / 1e9, 1)}
+        if fma and peaks:
+            # against min(measured DFMA rate, AI x HBM); the operands are
+            # L2-resident, so these calls are latency-bound and the fraction
+            # is given for information
+            tf = flops[name] / (dev_us / 1e6) / 1e12
+            att = attainable(flops[name], byts, fma["fp64_tflops"], peaks["hbm_gbs"])
+            rec.update({"TFLOP/s_device": round(tf, 4), "attainable_TFLOP/s": round(att, 3),
+                        "frac_of_attainable": round(tf / att, 4)})
         if with_oracle:
             t0 = time.perf_counter()
             for _ in range(3):

@@ -273,6 +273,20 @@ int tl_device_status(void* stream);
 int tl_selftest_wait_timeout(double limit_us, void* stream);
 
 /*
+ * tl_fma_peak_probe -- measurement helper with no counterpart in the paper:
+ * enqueues one kernel that keeps every SM's FP32 FMA (dtype TL_F32) or FP64
+ * DFMA (TL_F64) pipes busy with independent fused multiply-adds, `iters`
+ * per chain (a positive multiple of 16), and writes the floating-point
+ * operations it performs (2 per FMA) to *flops (host).  Timing it with
+ * events on `stream` gives the device's measured FMA rate, the peak that
+ * FP32 SIMT and FP64 operations are compared against.  sink: device pointer
+ * to one element of the dtype (written only for a result no chain reaches,
+ * so the arithmetic cannot be optimised away).  Changes no device setting.
+ * Errors: TL_EINVAL (dtype, iters, null pointers), TL_ECUDA.
+ */
+int tl_fma_peak_probe(int32_t dtype, int64_t iters, void* sink, double* flops, void* stream);
+
+/*
  * tl_view -- host-only: the descriptor of a view of A (Sec. 3.3): for every
  * mode r a range with first index f[r], step t[r] and last index l[r]
  * (inclusive), 0 <= f[r] <= l[r] < n_r and t[r] >= 1.  The view has extents

@@ -182,6 +182,8 @@ def _declare(_lib):
     _lib.tl_batch_set_variant.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int64, ctypes.c_void_p]
     _lib.tl_selftest_wait_timeout.argtypes = [ctypes.c_double, ctypes.c_void_p]
+    _lib.tl_fma_peak_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
     _lib.tl_ttvs.argtypes = [_T, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_uint32),
                              ctypes.c_uint32, _T, ctypes.c_void_p]
     _lib.tl_ttms.argtypes = [_T, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64),
@@ -358,6 +360,14 @@ def tl_batch_run(batch, stream=None) -> int:
 
 def tl_batch_destroy(batch) -> int:
     return _lib.tl_batch_destroy(batch)
+
+
+def tl_fma_peak_probe(dtype: int, iters: int, sink, stream=None) -> tuple:
+    """Enqueues the FMA throughput probe; returns (rc, flops it performs)."""
+    f = ctypes.c_double(0.0)
+    rc = _lib.tl_fma_peak_probe(int(dtype), int(iters), _addr(sink), ctypes.byref(f),
+                                _stream(stream))
+    return rc, f.value
 
 
 def tl_batch_describe(batch) -> tuple:
