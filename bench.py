@@ -70,7 +70,7 @@ def parse_args():
     ap.add_argument("--no-small", action="store_true",
                     help="skip the small FP64 64^3 latency measurements")
     ap.add_argument("--batch-ops", type=int, default=4096)
-    ap.add_argument("--serve-requests", type=int, default=3000)
+    ap.add_argument("--serve-requests", type=int, default=100000)
     ap.add_argument("--serve-rates", default="2000,10000,40000")
     return ap.parse_args()
 
@@ -775,10 +775,12 @@ def measure_batch(tl, torch, dev, sh, nops, reps=5):
 
 # -------------------------------------------------------------- serving ---
 
-def measure_serve(tl, torch, dev, sh, nreq, rates, pool=192, budget=40_000_000_000):
+def measure_serve(tl, torch, dev, sh, nreq, rates, pool=1024, budget=40_000_000_000, streams=8):
     """Poisson stream of ttv / ttm / entrywise requests (order 2-7, lognormal
-    element counts over 1e3-1e8, 20% FP64) on device-resident operands:
-    continuous batching against serving one request at a time."""
+    element counts over 1e3-1e8, 20% FP64) drawn from a pool of `pool`
+    device-resident requests: continuous batching (`streams` streams, 40 GB
+    admission budget) against serving one request at a time on one stream,
+    over the same arrival trace of `nreq` requests per offered rate."""
     import synth
     reqs = synth.serving_stream(pool, 1.0, seed=synth.BASE_SEED + 5)
     keep, ops, calls, sizes = [], [], [], []
@@ -828,13 +830,14 @@ def measure_serve(tl, torch, dev, sh, nreq, rates, pool=192, budget=40_000_000_0
     def pct(x, p):
         return float(np.percentile(np.asarray(x), p)) if x else None
 
-    out = {"pool_requests": pool, "requests_per_rate": nreq, "budget_bytes": budget, "rates": []}
+    out = {"pool_requests": pool, "requests_per_rate": nreq, "budget_bytes": budget,
+           "streams": streams, "rates": []}
     for rate in rates:
         g = synth.rng(int(rate))
         pick = g.integers(0, pool, size=nreq)
         arr = np.cumsum(g.exponential(1.0 / rate, size=nreq))
         # ---- continuous batching server
-        rc, ctx = tl.tl_ctx_create(budget, 4, tl.TL_CTX_PERSISTENT)
+        rc, ctx = tl.tl_ctx_create(budget, streams, tl.TL_CTX_PERSISTENT)
         tl.check(rc, "tl_ctx_create")
         tickets, sub_lag = [], []
         t0 = time.perf_counter()
@@ -856,8 +859,8 @@ def measure_serve(tl, torch, dev, sh, nreq, rates, pool=192, budget=40_000_000_0
         rc, maxin, batches, completed = tl.tl_ctx_stats(ctx)
         tl.tl_ctx_destroy(ctx)
         served = {"ops/s": round(nreq / t_end, 1), "p50_ms": round(pct(lat, 50), 3),
-                  "p99_ms": round(pct(lat, 99), 3), "batches": batches,
-                  "max_inflight_GB": round(maxin / 1e9, 3)}
+                  "p99_ms": round(pct(lat, 99), 3), "batches": batches, "requests": nreq,
+                  "seconds": round(t_end, 2), "max_inflight_GB": round(maxin / 1e9, 3)}
         # ---- plain: one request at a time, synchronously, on one stream
         lat_p = []
         t0 = time.perf_counter()
@@ -871,7 +874,8 @@ def measure_serve(tl, torch, dev, sh, nreq, rates, pool=192, budget=40_000_000_0
             lat_p.append((time.perf_counter() - t0 - arr[i]) * 1e3)
         t_end_p = time.perf_counter() - t0
         plain = {"ops/s": round(nreq / t_end_p, 1), "p50_ms": round(pct(lat_p, 50), 3),
-                 "p99_ms": round(pct(lat_p, 99), 3)}
+                 "p99_ms": round(pct(lat_p, 99), 3), "requests": nreq,
+                 "seconds": round(t_end_p, 2)}
         out["rates"].append({"offered_ops/s": rate, "served": served, "plain": plain})
     return out
 

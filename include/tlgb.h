@@ -402,8 +402,12 @@ typedef struct tl_ctx tl_ctx;
  * bounds the bytes of operands and outputs of requests admitted but not yet
  * completed (requests beyond it wait; a single request larger than the
  * budget is rejected with TL_ENOMEM), `streams` (>= 1) device streams carry
- * concurrent batches.  The context owns its streams, descriptor tables and
- * workspace and allocates them here.
+ * concurrent batches of small requests, at the highest stream priority; one
+ * more stream, at the lowest priority, runs requests of 16 MB or more one at
+ * a time (small requests queued behind one pass it).  Requests are admitted
+ * in arrival order within each of the two classes, and a batch holds at most
+ * 256 operations and 64 MB.  The context owns its streams, descriptor tables
+ * and workspace and allocates them here.
  */
 int tl_ctx_create(size_t budget_bytes, int32_t streams, int32_t flags, tl_ctx** out);
 int tl_ctx_destroy(tl_ctx* ctx);

@@ -641,6 +641,10 @@ struct Batch {
     size_t bytes = 0;            // algorithmic bytes of all operations
     int direct = 0;              // operations run by their own kernels
     std::vector<tl_op> direct_ops;
+    // the direct operations run on a stream of their own, concurrently with
+    // the persistent launch, between a fork and a join event
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 // Operations the persistent kernel does not take: a contraction this long
@@ -748,15 +752,21 @@ static int fill_op(const tl_op& o, BOp& b, size_t& bytes, bool& direct)
 }
 
 // Times one candidate on a one-operation table (milliseconds, best of 3).
-static float time_candidate(const BOp& op, Candidate c, BOp* dev_one, unsigned long long* counter,
-                            cudaStream_t st)
+// Device time of one persistent launch over `ops` (their variants and unit
+// sizes as assigned; ubegin is recomputed here): the best of 3 launches after
+// one warm-up.  dev holds room for ops.size() descriptors.
+static float time_ops(std::vector<BOp>& ops, BOp* dev, unsigned long long* counter,
+                      cudaStream_t st)
 {
-    BOp t = op;
-    t.variant = c.variant;
-    t.unit = c.unit;
-    t.ubegin = 0;
-    const int64_t units = units_of(t);
-    cudaMemcpyAsync(dev_one, &t, sizeof t, cudaMemcpyHostToDevice, st);
+    int64_t units = 0;
+    for (BOp& b : ops) {
+        b.ubegin = units;
+        units += units_of(b);
+    }
+    if (units == 0) return 0.f;
+    if (cudaMemcpyAsync(dev, ops.data(), sizeof(BOp) * ops.size(), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return 1e30f;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -765,7 +775,7 @@ static float time_candidate(const BOp& op, Candidate c, BOp* dev_one, unsigned l
     for (int rep = 0; rep < 4; ++rep) {
         cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
         cudaEventRecord(e0, st);
-        batch_kernel<<<grid, kThreads, 0, st>>>(dev_one, 1, units, counter);
+        batch_kernel<<<grid, kThreads, 0, st>>>(dev, (int)ops.size(), units, counter);
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         float ms = 0;
@@ -774,6 +784,7 @@ static float time_candidate(const BOp& op, Candidate c, BOp* dev_one, unsigned l
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaGetLastError();
     return best;
 }
 
@@ -799,65 +810,81 @@ int batch_create(const tl_op* ops, size_t count, int32_t flags, void* stream, Ba
         }
         if (b.count > 0) B->host.push_back(b);
     }
-    // variant and unit size per operation
-    std::map<std::string, Candidate> chosen;
-    if (flags & TL_BATCH_TUNE) {
-        std::lock_guard<std::mutex> lk(g_tune.mu);
-        g_tune.load();
-        const std::string tag = device_tag();
-        // representative = largest operation of each class
-        std::map<std::string, const BOp*> rep;
-        for (const BOp& b : B->host) {
-            std::string k = tag + "|" + class_key(b);
-            auto it = rep.find(k);
-            if (it == rep.end() || it->second->count < b.count) rep[k] = &b;
-        }
-        BOp* dev_one = nullptr;
-        unsigned long long* ctr = nullptr;
-        bool tuned = false;
-        for (auto& kv : rep) {
-            auto hit = g_tune.table.find(kv.first);
-            if (hit != g_tune.table.end()) {
-                chosen[kv.first] = hit->second;
-                continue;
-            }
-            if (!dev_one) {
-                if (cudaMalloc(&dev_one, sizeof(BOp)) != cudaSuccess ||
-                    cudaMalloc(&ctr, sizeof(unsigned long long)) != cudaSuccess) {
-                    cudaGetLastError();
-                    break;
-                }
-            }
-            Candidate best = heuristic(*kv.second);
-            float best_ms = 1e30f;
-            for (Candidate c : candidates(*kv.second)) {
-                float ms = time_candidate(*kv.second, c, dev_one, ctr, st);
-                if (ms < best_ms) { best_ms = ms; best = c; }
-            }
-            chosen[kv.first] = best;
-            g_tune.table[kv.first] = best;
-            tuned = true;
-        }
-        if (dev_one) cudaFree(dev_one);
-        if (ctr) cudaFree(ctr);
-        if (tuned) g_tune.save();
-        for (BOp& b : B->host) {
-            auto it = chosen.find(tag + "|" + class_key(b));
-            Candidate c = it != chosen.end() ? sanitize(it->second, b) : heuristic(b);
-            b.variant = c.variant;
-            b.unit = c.unit;
-        }
-    } else {
-        for (BOp& b : B->host) {
-            Candidate c = heuristic(b);
-            b.variant = c.variant;
-            b.unit = c.unit;
-        }
-    }
     // large operations first, so the tail of the persistent launch is small units
     std::stable_sort(B->host.begin(), B->host.end(),
                      [](const BOp& x, const BOp& y) { return x.count * (x.kind == TL_OP_TTM ? x.J : 1) >
                                                              y.count * (y.kind == TL_OP_TTM ? y.J : 1); });
+    // variant and unit size per operation: the default choice, or with
+    // TL_BATCH_TUNE the choice of each shape class timed on all of the
+    // batch's operations of that class launched together (cached on disk);
+    // the tuned plan is kept only if the whole batch runs faster with it
+    for (BOp& b : B->host) {
+        const Candidate c = heuristic(b);
+        b.variant = c.variant;
+        b.unit = c.unit;
+    }
+    if ((flags & TL_BATCH_TUNE) && !B->host.empty()) {
+        std::lock_guard<std::mutex> lk(g_tune.mu);
+        g_tune.load();
+        const std::string tag = device_tag();
+        std::map<std::string, std::vector<size_t>> members;
+        for (size_t i = 0; i < B->host.size(); ++i)
+            members[tag + "|" + class_key(B->host[i])].push_back(i);
+        size_t largest = 0;
+        for (auto& kv : members) largest = std::max(largest, kv.second.size());
+        BOp* dev = nullptr;
+        unsigned long long* ctr = nullptr;
+        if (cudaMalloc(&dev, sizeof(BOp) * B->host.size()) != cudaSuccess ||
+            cudaMalloc(&ctr, sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            if (dev) cudaFree(dev);
+            batch_destroy(B);
+            return TL_ENOMEM;
+        }
+        std::vector<BOp> tuned = B->host;
+        bool saved = false;
+        std::vector<BOp> sub;
+        for (auto& kv : members) {
+            Candidate pick;
+            auto hit = g_tune.table.find(kv.first);
+            if (hit != g_tune.table.end()) {
+                pick = hit->second;
+            } else {
+                const BOp& rep = B->host[kv.second.front()];
+                pick = heuristic(rep);
+                float best_ms = 1e30f;
+                for (Candidate c : candidates(rep)) {
+                    sub.clear();
+                    for (size_t i : kv.second) {
+                        BOp t = B->host[i];
+                        const Candidate s_ = sanitize(c, t);
+                        t.variant = s_.variant;
+                        t.unit = s_.unit;
+                        sub.push_back(t);
+                    }
+                    const float ms = time_ops(sub, dev, ctr, st);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        pick = c;
+                    }
+                }
+                g_tune.table[kv.first] = pick;
+                saved = true;
+            }
+            for (size_t i : kv.second) {
+                const Candidate s_ = sanitize(pick, tuned[i]);
+                tuned[i].variant = s_.variant;
+                tuned[i].unit = s_.unit;
+            }
+        }
+        if (saved) g_tune.save();
+        std::vector<BOp> plain = B->host;
+        const float t_plain = time_ops(plain, dev, ctr, st);
+        const float t_tuned = time_ops(tuned, dev, ctr, st);
+        if (t_tuned < t_plain) B->host = tuned;
+        cudaFree(dev);
+        cudaFree(ctr);
+    }
     int64_t u = 0;
     for (BOp& b : B->host) {
         b.ubegin = u;
@@ -893,22 +920,47 @@ static int enqueue(Batch* B, cudaStream_t st)
     return TL_OK;
 }
 
+int batch_launch(Batch* B, cudaStream_t st);
+
 int batch_run(Batch* B, void* stream)
 {
     if (!B) return TL_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // operations the batch kernel does not take run through their own kernels
+    // operations the batch kernel does not take run through their own kernels,
+    // on the side stream when there is a persistent launch to overlap them with
+    const bool overlap = !B->direct_ops.empty() && B->total_units > 0;
+    if (overlap && !B->side) {
+        if (cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->join, cudaEventDisableTiming) != cudaSuccess)
+            return TL_ECUDA;
+    }
+    void* dstream = overlap ? static_cast<void*>(B->side) : stream;
+    if (overlap && (cudaEventRecord(B->fork, st) != cudaSuccess ||
+                    cudaStreamWaitEvent(B->side, B->fork, 0) != cudaSuccess))
+        return TL_ECUDA;
     for (const tl_op& o : B->direct_ops) {
         int rc = TL_OK;
-        if (o.kind == TL_OP_TTV) rc = tl_ttv(&o.A, o.vec, o.incb, o.q, &o.C, o.accumulate, stream);
+        if (o.kind == TL_OP_TTV) rc = tl_ttv(&o.A, o.vec, o.incb, o.q, &o.C, o.accumulate, dstream);
         else if (o.kind == TL_OP_TTM)
-            rc = tl_ttm(&o.A, o.vec, o.J, o.ldb_row, o.ldb_col, o.q, &o.C, o.precision, o.accumulate, stream);
+            rc = tl_ttm(&o.A, o.vec, o.J, o.ldb_row, o.ldb_col, o.q, &o.C, o.precision, o.accumulate,
+                        dstream);
         else
             rc = tl_entrywise(o.entry_op, &o.A,
                               (o.entry_op == TL_COPY || o.entry_op == TL_SCALE) ? nullptr : &o.B,
-                              o.alpha, &o.C, stream);
+                              o.alpha, &o.C, dstream);
         if (rc) return rc;
     }
+    if (overlap && cudaEventRecord(B->join, B->side) != cudaSuccess) return TL_ECUDA;
+    int rc = batch_launch(B, st);
+    // the caller's stream waits for the direct operations as well
+    if (overlap && cudaStreamWaitEvent(st, B->join, 0) != cudaSuccess) return TL_ECUDA;
+    return rc;
+}
+
+// The persistent launch of a batch on st (from its CUDA graph when asked).
+int batch_launch(Batch* B, cudaStream_t st)
+{
     if (B->total_units == 0) return TL_OK;
     if (!(B->flags & TL_BATCH_GRAPH)) {
         int rc = enqueue(B, st);
@@ -939,6 +991,12 @@ int batch_run(Batch* B, void* stream)
 int batch_destroy(Batch* B)
 {
     if (!B) return TL_OK;
+    if (B->side) {
+        cudaStreamSynchronize(B->side);
+        cudaStreamDestroy(B->side);
+    }
+    if (B->fork) cudaEventDestroy(B->fork);
+    if (B->join) cudaEventDestroy(B->join);
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
     if (B->dev_ops) cudaFree(B->dev_ops);

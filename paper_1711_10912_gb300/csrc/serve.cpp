@@ -7,12 +7,16 @@
 //      each request's submission-to-completion latency and returning its
 //      bytes to the budget),
 //   2. admits queued requests in arrival order while their operand + output
-//      bytes fit in the budget, and
-//   3. launches everything admitted as one batch on a free stream slot: one
-//      persistent launch (TL_CTX_PERSISTENT) or one launch per operation.
+//      bytes fit in the budget, grouped into batches of bounded size (a large
+//      request is a batch of its own), and
+//   3. launches each batch on a free stream slot: one persistent launch
+//      (TL_CTX_PERSISTENT) or one launch per operation.
 // Requests that arrive while earlier batches run are admitted as soon as a
 // slot and budget free up, so work from different requests overlaps on the
-// device.  Nothing here waits on the GPU while holding the context lock.
+// device.  While batches are in flight the worker polls their completion
+// events without sleeping, so completion is seen within microseconds; when
+// idle it sleeps until a submission.  Nothing here waits on the GPU while
+// holding the context lock.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -118,6 +122,72 @@ namespace tl {
 namespace {
 
 constexpr size_t kSlotCapacity = 8192;     // operations per persistent launch
+// Batch formation: a request of kLargeBytes or more runs as a batch of its own
+// (on its own stream, so small requests keep flowing on the others); small
+// requests are grouped up to kBatchOps operations and kBatchBytes, so that a
+// batch completes (and releases its requests) within tens of microseconds
+// instead of holding every queued request until the whole queue is done.
+constexpr size_t kLargeBytes = size_t(16) << 20;
+constexpr size_t kBatchBytes = size_t(64) << 20;
+constexpr size_t kBatchOps = 256;
+
+// Marks every request of a retired slot complete; returns true if any was.
+bool retire(tl_ctx* c)
+{
+    bool progress = false;
+    for (SlotState& s : c->slots) {
+        if (!s.busy) continue;
+        cudaError_t q = cudaEventQuery(s.done);
+        if (q == cudaErrorNotReady) continue;
+        const auto now = Clock::now();
+        for (Request* r : s.reqs) {
+            r->status = (q == cudaSuccess) ? TL_OK : TL_ECUDA;
+            r->latency_ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
+            c->inflight_bytes -= r->bytes;
+            c->completed++;
+        }
+        if (q != cudaSuccess) cudaGetLastError();
+        s.reqs.clear();
+        s.busy = false;
+        progress = true;
+    }
+    return progress;
+}
+
+// Takes the next batch off the queue in arrival order, admitting each taken
+// request against the budget.  large_lane: the first large request (one of
+// kLargeBytes or more) alone.  Otherwise: consecutive small requests within
+// the batch caps, passing over large requests, which wait for the large lane.
+// Empty when nothing can be admitted.
+std::vector<Request*> take_batch(tl_ctx* c, bool large_lane)
+{
+    std::vector<Request*> take;
+    size_t ops = 0, bytes = 0;
+    for (auto it = c->pending.begin(); it != c->pending.end();) {
+        Request* r = *it;
+        if (r->cancelled) {
+            it = c->pending.erase(it);
+            continue;
+        }
+        const bool large = r->bytes >= kLargeBytes;
+        if (large != large_lane) {
+            // the large lane looks for the first large request; a batch of
+            // small requests passes over large ones (they wait for the lane)
+            ++it;
+            continue;
+        }
+        if (c->inflight_bytes + r->bytes > c->budget && c->inflight_bytes > 0) break;
+        if (!take.empty() && (ops + r->ops.size() > kBatchOps || bytes + r->bytes > kBatchBytes))
+            break;
+        it = c->pending.erase(it);
+        c->inflight_bytes += r->bytes;
+        ops += r->ops.size();
+        bytes += r->bytes;
+        take.push_back(r);
+        if (large) break;
+    }
+    return take;
+}
 
 void run_worker(tl_ctx* c)
 {
@@ -125,58 +195,38 @@ void run_worker(tl_ctx* c)
     std::vector<const tl_op*> batch_ops;
     std::unique_lock<std::mutex> lk(c->mu);
     while (!c->stop) {
-        bool progress = false;
         // 1. retire completed batches
-        for (SlotState& s : c->slots) {
-            if (!s.busy) continue;
-            cudaError_t q = cudaEventQuery(s.done);
-            if (q == cudaErrorNotReady) continue;
-            const auto now = Clock::now();
-            for (Request* r : s.reqs) {
-                r->status = (q == cudaSuccess) ? TL_OK : TL_ECUDA;
-                r->latency_ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
-                c->inflight_bytes -= r->bytes;
-                c->completed++;
-            }
-            if (q != cudaSuccess) cudaGetLastError();
-            s.reqs.clear();
-            s.busy = false;
-            progress = true;
-        }
-        if (progress) c->cv.notify_all();
-        // 2. admit queued requests onto a free slot
-        SlotState* free_slot = nullptr;
-        for (SlotState& s : c->slots)
-            if (!s.busy) { free_slot = &s; break; }
-        if (free_slot && !c->pending.empty()) {
+        if (retire(c)) c->cv.notify_all();
+        // 2. admit queued requests onto every free slot: the last slot is the
+        //    large-request lane (low stream priority, one request at a time),
+        //    the others take batches of small requests (high priority)
+        for (;;) {
+            SlotState* free_slot = nullptr;
             std::vector<Request*> take;
-            size_t ops = 0;
-            while (!c->pending.empty()) {
-                Request* r = c->pending.front();
-                if (r->cancelled) {
-                    c->pending.pop_front();
-                    continue;
-                }
-                if (c->inflight_bytes + r->bytes > c->budget && !take.empty()) break;
-                if (c->inflight_bytes + r->bytes > c->budget && c->inflight_bytes > 0) break;
-                if (ops + r->ops.size() > kSlotCapacity && !take.empty()) break;
-                c->pending.pop_front();
-                c->inflight_bytes += r->bytes;
-                ops += r->ops.size();
-                take.push_back(r);
+            SlotState& lane = c->slots.back();
+            if (!lane.busy && !c->pending.empty()) {
+                take = take_batch(c, true);
+                if (!take.empty()) free_slot = &lane;
             }
-            if (!take.empty()) {
-                if (c->inflight_bytes > c->max_inflight) c->max_inflight = c->inflight_bytes;
-                c->batches++;
-                free_slot->busy = true;
-                free_slot->reqs = take;
-                batch_ops.clear();
-                for (Request* r : take)
-                    for (auto& o : r->ops) batch_ops.push_back(&o->op);
-                // 3. launch without holding the lock
-                lk.unlock();
+            if (take.empty()) {
+                for (size_t i = 0; i + 1 < c->slots.size(); ++i)
+                    if (!c->slots[i].busy) { free_slot = &c->slots[i]; break; }
+                if (!free_slot || c->pending.empty()) break;
+                take = take_batch(c, false);
+            }
+            if (take.empty()) break;
+            if (c->inflight_bytes > c->max_inflight) c->max_inflight = c->inflight_bytes;
+            c->batches++;
+            free_slot->busy = true;
+            free_slot->reqs = take;
+            batch_ops.clear();
+            for (Request* r : take)
+                for (auto& o : r->ops) batch_ops.push_back(&o->op);
+            // 3. launch without holding the lock
+            lk.unlock();
+            int rc;
+            {
                 NvtxRange nvtx_range("tl_ctx_batch_launch");
-                int rc;
                 if (c->flags & TL_CTX_PERSISTENT) {
                     rc = slot_launch(free_slot->table, batch_ops.data(), batch_ops.size(),
                                      free_slot->stream);
@@ -191,28 +241,36 @@ void run_worker(tl_ctx* c)
                 }
                 if (rc == TL_OK && cudaEventRecord(free_slot->done, free_slot->stream) != cudaSuccess)
                     rc = TL_ECUDA;
-                lk.lock();
-                if (rc != TL_OK) {
-                    // the launch failed on the host: the requests fail, the slot frees
-                    cudaStreamSynchronize(free_slot->stream);
-                    cudaGetLastError();
-                    for (Request* r : take) {
-                        r->status = rc;
-                        r->latency_ms = std::chrono::duration<double, std::milli>(
-                                            Clock::now() - r->t_submit).count();
-                        c->inflight_bytes -= r->bytes;
-                    }
-                    free_slot->reqs.clear();
-                    free_slot->busy = false;
-                    c->cv.notify_all();
+            }
+            lk.lock();
+            if (rc != TL_OK) {
+                // the launch failed on the host: the requests fail, the slot frees
+                cudaStreamSynchronize(free_slot->stream);
+                cudaGetLastError();
+                for (Request* r : take) {
+                    r->status = rc;
+                    r->latency_ms = std::chrono::duration<double, std::milli>(
+                                        Clock::now() - r->t_submit).count();
+                    c->inflight_bytes -= r->bytes;
                 }
-                continue;
+                free_slot->reqs.clear();
+                free_slot->busy = false;
+                c->cv.notify_all();
             }
         }
         bool any_busy = false;
         for (SlotState& s : c->slots) any_busy |= s.busy;
-        // sleep until a submission arrives, or briefly while batches run
-        c->cv.wait_for(lk, any_busy ? std::chrono::microseconds(20) : std::chrono::milliseconds(2));
+        if (any_busy) {
+            // work in flight: poll its completion without sleeping (letting
+            // submitters take the lock between polls), so a finished batch
+            // is seen within microseconds
+            lk.unlock();
+            std::this_thread::yield();
+            lk.lock();
+        } else {
+            // idle: sleep until a submission arrives
+            c->cv.wait_for(lk, std::chrono::milliseconds(2));
+        }
     }
 }
 
@@ -234,9 +292,19 @@ int tl_ctx_create(size_t budget_bytes, int32_t streams, int32_t flags, tl_ctx** 
     }
     c->flags = flags;
     c->budget = budget_bytes;
-    c->slots.resize(streams);
-    for (SlotState& s : c->slots) {
-        bool ok = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess &&
+    // `streams` slots for batches of small requests at the highest stream
+    // priority, plus one lane for large requests at the lowest, so that
+    // small work is scheduled first whenever SMs free up
+    c->slots.resize((size_t)streams + 1);
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        least = greatest = 0;
+    }
+    for (size_t i = 0; i < c->slots.size(); ++i) {
+        SlotState& s = c->slots[i];
+        const int prio = i + 1 == c->slots.size() ? least : greatest;
+        bool ok = cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, prio) == cudaSuccess &&
                   cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) == cudaSuccess;
         if (ok && (flags & TL_CTX_PERSISTENT)) {
             s.table = slot_create(kSlotCapacity);
