@@ -13,9 +13,10 @@
 //      (TL_CTX_PERSISTENT) or one launch per operation.
 // Requests that arrive while earlier batches run are admitted as soon as a
 // slot and budget free up, so work from different requests overlaps on the
-// device.  While batches are in flight the worker polls their completion
-// events without sleeping, so completion is seen within microseconds; when
-// idle it sleeps until a submission.  Nothing here waits on the GPU while
+// device.  While batches are in flight, and for a few milliseconds after the
+// last one, the worker polls without sleeping, so completions and new
+// requests are seen within microseconds; when idle longer it sleeps until a
+// submission.  Nothing here waits on the GPU while
 // holding the context lock.
 #include <cuda_runtime.h>
 
@@ -130,6 +131,9 @@ constexpr size_t kSlotCapacity = 8192;     // operations per persistent launch
 constexpr size_t kLargeBytes = size_t(16) << 20;
 constexpr size_t kBatchBytes = size_t(64) << 20;
 constexpr size_t kBatchOps = 256;
+// After the last request completes the worker keeps polling this long before
+// it sleeps (one host core busy while requests keep arriving).
+constexpr int kSpinMs = 5;
 
 // Marks every request of a retired slot complete; returns true if any was.
 bool retire(tl_ctx* c)
@@ -194,6 +198,7 @@ void run_worker(tl_ctx* c)
     cudaSetDevice(c->device);
     std::vector<const tl_op*> batch_ops;
     std::unique_lock<std::mutex> lk(c->mu);
+    auto last_active = Clock::now();
     while (!c->stop) {
         // 1. retire completed batches
         if (retire(c)) c->cv.notify_all();
@@ -260,10 +265,13 @@ void run_worker(tl_ctx* c)
         }
         bool any_busy = false;
         for (SlotState& s : c->slots) any_busy |= s.busy;
-        if (any_busy) {
-            // work in flight: poll its completion without sleeping (letting
-            // submitters take the lock between polls), so a finished batch
-            // is seen within microseconds
+        const auto now = Clock::now();
+        if (any_busy || !c->pending.empty()) last_active = now;
+        if (now - last_active < std::chrono::milliseconds(kSpinMs)) {
+            // work in flight, or some in the last few milliseconds: poll
+            // without sleeping (letting submitters take the lock between
+            // polls), so a finished batch or a new request is seen within
+            // microseconds rather than after a thread wake-up
             lk.unlock();
             std::this_thread::yield();
             lk.lock();
