@@ -54,6 +54,7 @@ extern "C" {
 #define TL_ECUDA        -4   /* a CUDA launch or runtime call failed */
 #define TL_ETIMEOUT     -5   /* a bounded device wait gave up */
 #define TL_ECANCELED    -6   /* request cancelled or failed by the host */
+#define TL_EBOUNDS      -7   /* bounds-checked builds only: a mapped offset left its operand */
 #define TL_PENDING       1   /* tl_poll: the request has not completed yet */
 
 #define TL_MAX_ORDER 16
@@ -249,6 +250,20 @@ const char* tl_strerror(int code);
 /* Library version (major*10000 + minor*100 + patch). */
 int tl_version(void);
 
+/*
+ * tl_bounds_checked -- 1 for the bounds-checked debug build of the library
+ * (built with TL_CHECK_BOUNDS, libtlgb_checked.so), 0 for the product build.
+ * In the checked build every offset that the kernels' index mappers produce
+ * (the first element of each row, fiber or vector a thread touches, for
+ * every operand) is compared with that operand's extent in memory, less the
+ * accesses the plan adds along the contraction (A) or the output column (C
+ * of ttm); an offset outside is recorded, replaced by 0 (the access stays
+ * inside the operand) and reported by tl_device_status() as TL_EBOUNDS.
+ * Kernels that address memory through TMA tensor maps (the tensor-core ttm,
+ * the TMA entrywise tiles) are bounded by the maps' extents instead.
+ */
+int tl_bounds_checked(void);
+
 /* Number of kernels this library has launched in this process (all devices,
    all streams), for launch accounting in benchmarks. */
 uint64_t tl_launch_count(void);
@@ -256,7 +271,8 @@ uint64_t tl_launch_count(void);
 /*
  * tl_device_status -- synchronises `stream`, then reports whether any
  * bounded device-side wait of the library's pipelined kernels gave up since
- * the last call: TL_ETIMEOUT (and the flag is cleared) or TL_OK.  Such a
+ * the last call: TL_ETIMEOUT (and the flag is cleared) or TL_OK; in the
+ * bounds-checked build also TL_EBOUNDS (see tl_bounds_checked).  Such a
  * kernel does not hang: after about two seconds without progress it records
  * the timeout, drains its own copies, frees its tensor memory and returns,
  * leaving its output incomplete.

@@ -18,7 +18,9 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtlgb.so")
+# TL_LIBRARY selects another build of the library (the bounds-checked
+# libtlgb_checked.so, for instance); the default is the product build.
+LIB_PATH = os.environ.get("TL_LIBRARY") or os.path.join(_HERE, "libtlgb.so")
 
 
 class _MissingLibrary:
@@ -36,6 +38,7 @@ _lib = _MissingLibrary()
 TL_OK, TL_EINVAL, TL_EUNSUPPORTED, TL_ENOMEM, TL_ECUDA, TL_ETIMEOUT, TL_ECANCELED = \
     0, -1, -2, -3, -4, -5, -6
 TL_PENDING = 1
+TL_EBOUNDS = -7
 TL_F32, TL_F64 = 0, 1
 TL_P_DEFAULT, TL_P_F64, TL_P_F32, TL_P_TF32, TL_P_BF16, TL_P_BF16X3 = range(6)
 TL_ADD, TL_SUB, TL_MUL, TL_DIV, TL_COPY, TL_SCALE = range(6)
@@ -182,6 +185,7 @@ def _declare(_lib):
     _lib.tl_batch_set_variant.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int64, ctypes.c_void_p]
     _lib.tl_selftest_wait_timeout.argtypes = [ctypes.c_double, ctypes.c_void_p]
+    _lib.tl_bounds_checked.restype = ctypes.c_int
     _lib.tl_fma_peak_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
     _lib.tl_ttvs.argtypes = [_T, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_uint32),
@@ -360,6 +364,11 @@ def tl_batch_run(batch, stream=None) -> int:
 
 def tl_batch_destroy(batch) -> int:
     return _lib.tl_batch_destroy(batch)
+
+
+def tl_bounds_checked() -> int:
+    """1 if the loaded library is the bounds-checked debug build."""
+    return int(_lib.tl_bounds_checked())
 
 
 def tl_fma_peak_probe(dtype: int, iters: int, sink, stream=None) -> tuple:

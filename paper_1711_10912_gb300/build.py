@@ -21,7 +21,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtlgb.so")
-STAMP = os.path.join(BUILD, "libtlgb.stamp")
+# the bounds-checked debug build (TL_CHECK_BOUNDS): every offset the index
+# mappers produce is checked against its operand's extent; never the product
+CHECKED_BUILD = os.path.join(ROOT, "_build_checked")
+CHECKED_LIB = os.path.join(HERE, "libtlgb_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -46,8 +49,9 @@ def sources():
     return out
 
 
-def _digest(srcs) -> str:
+def _digest(srcs, extra=()) -> str:
     h = hashlib.sha256()
+    h.update(" ".join(extra).encode())
     for f in sorted(os.listdir(CSRC)) + [os.path.join("..", "..", "include", "tlgb.h")]:
         path = os.path.join(CSRC, f)
         if os.path.isfile(path):
@@ -59,12 +63,13 @@ def _digest(srcs) -> str:
     return h.hexdigest()
 
 
-def _compile(src: str, verbose: bool):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, verbose: bool, build_dir: str = BUILD, extra=()):
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     if src.endswith(".cu"):
-        cmd = [_nvcc(), "-c", src, "-o", obj, "-I", CSRC, "-I", INCLUDE] + NVCC_FLAGS
+        cmd = [_nvcc(), "-c", src, "-o", obj, "-I", CSRC, "-I", INCLUDE] + NVCC_FLAGS + list(extra)
     else:
-        cmd = ["g++", "-c", src, "-o", obj, "-I", CSRC, "-I", INCLUDE, "-I", _cuda_include()] + CXX_FLAGS
+        cmd = (["g++", "-c", src, "-o", obj, "-I", CSRC, "-I", INCLUDE, "-I", _cuda_include()] +
+               CXX_FLAGS + list(extra))
     res = subprocess.run(cmd, capture_output=True, text=True)
     log = res.stdout + res.stderr
     if res.returncode != 0:
@@ -74,31 +79,38 @@ def _compile(src: str, verbose: bool):
     return obj, log
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compiles and links libtlgb.so if the sources changed; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compiles and links libtlgb.so (or, with checked=True, the
+    bounds-checked libtlgb_checked.so) if the sources changed; returns its
+    path."""
+    build_dir = CHECKED_BUILD if checked else BUILD
+    lib = CHECKED_LIB if checked else LIB
+    stamp = os.path.join(build_dir, os.path.basename(lib) + ".stamp")
+    extra = ["-DTL_CHECK_BOUNDS"] if checked else []
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sources()
-    dig = _digest(srcs)
-    if not force and os.path.exists(LIB) and os.path.exists(STAMP):
-        with open(STAMP) as fh:
+    dig = _digest(srcs, extra)
+    if not force and os.path.exists(lib) and os.path.exists(stamp):
+        with open(stamp) as fh:
             if fh.read().strip() == dig:
-                return LIB
+                return lib
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose), srcs))
+        results = list(ex.map(lambda s: _compile(s, verbose, build_dir, extra), srcs))
     objs = [o for o, _ in results]
-    with open(os.path.join(BUILD, "ptxas.log"), "w") as fh:
+    with open(os.path.join(build_dir, "ptxas.log"), "w") as fh:
         for o, log in results:
             fh.write(f"--- {os.path.basename(o)}\n{log}\n")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [_nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{res.stdout}{res.stderr}")
-    os.replace(tmp, LIB)
-    with open(STAMP, "w") as fh:
+    os.replace(tmp, lib)
+    with open(stamp, "w") as fh:
         fh.write(dig)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

@@ -59,6 +59,40 @@ int smem_optin(const void* func, int bytes)
     return TL_OK;
 }
 
+// Readers of the per-file bounds-violation words of builds with
+// TL_CHECK_BOUNDS (empty otherwise).
+namespace {
+std::mutex g_bounds_mu;
+std::vector<int (*)(bool)> g_bounds_readers;
+}  // namespace
+
+int register_bounds_reader(int (*reader)(bool))
+{
+    std::lock_guard<std::mutex> lk(g_bounds_mu);
+    g_bounds_readers.push_back(reader);
+    return 0;
+}
+
+int bounds_status(bool clear)
+{
+    std::lock_guard<std::mutex> lk(g_bounds_mu);
+    int rc = TL_OK;
+    for (auto* f : g_bounds_readers) {
+        const int r = f(clear);
+        if (r != TL_OK && rc == TL_OK) rc = r;
+    }
+    return rc;
+}
+
+bool bounds_checked_build()
+{
+#ifdef TL_CHECK_BOUNDS
+    return true;
+#else
+    return false;
+#endif
+}
+
 static std::atomic<uint64_t> g_launches{0};
 
 void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
@@ -222,6 +256,8 @@ extern "C" {
 
 int tl_version(void) { return 100; }
 
+int tl_bounds_checked(void) { return bounds_checked_build() ? 1 : 0; }
+
 uint64_t tl_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int tl_selftest_wait_timeout(double limit_us, void* stream)
@@ -237,8 +273,10 @@ int tl_device_status(void* stream)
     int a = ttm_tc_status(true);
     int b = ttv_status(true);
     int c = ew_status(true);
-    if (a == TL_ECUDA || b == TL_ECUDA || c == TL_ECUDA) return TL_ECUDA;
-    return (a == TL_ETIMEOUT || b == TL_ETIMEOUT || c == TL_ETIMEOUT) ? TL_ETIMEOUT : TL_OK;
+    int d = bounds_status(true);
+    if (a == TL_ECUDA || b == TL_ECUDA || c == TL_ECUDA || d == TL_ECUDA) return TL_ECUDA;
+    if (a == TL_ETIMEOUT || b == TL_ETIMEOUT || c == TL_ETIMEOUT) return TL_ETIMEOUT;
+    return d;
 }
 
 const char* tl_strerror(int code)
@@ -251,6 +289,7 @@ const char* tl_strerror(int code)
     case TL_ECUDA: return "CUDA error";
     case TL_ETIMEOUT: return "device wait timed out";
     case TL_ECANCELED: return "request cancelled";
+    case TL_EBOUNDS: return "a mapped offset fell outside its operand (bounds-checked build)";
     case TL_PENDING: return "pending";
     default: return "unknown error";
     }
@@ -322,6 +361,8 @@ static int norm_common(const Tensor& X, const Tensor* R, double* result, cudaStr
         d.s[2] = 0;
     }
     collapse(sp, 0);
+    sp.limit[0] = X.span();
+    sp.limit[1] = R ? R->span() : X.span();
     int nb = norm_partial_blocks(sp.count(), device_sms());
     double* partials = static_cast<double*>(workspace(st, sizeof(double) * 2 * (size_t)nb));
     if (!partials) return TL_ENOMEM;

@@ -64,7 +64,23 @@ struct BOp {
     void* C;
     int32_t idx32;       // every linear index fits 32 bits: decode with fd[]
     FastDiv fd[kBD];     // multiply-high division by n[d]
+    int64_t lim[3];      // operand limits (Space::limit), checked in bounds-checked builds
 };
+
+// Bounds-checked builds: a decoded offset outside its operand's limit is
+// recorded and replaced by 0 (product builds compile this away).
+__device__ __forceinline__ void bcheck(const BOp& op, int64_t& o0, int64_t& o1, int64_t& o2)
+{
+#ifdef TL_CHECK_BOUNDS
+    int64_t* o[3] = {&o0, &o1, &o2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (op.lim[k] > 0 && (*o[k] < 0 || *o[k] >= op.lim[k])) {
+            bounds_record(*o[k]);
+            *o[k] = 0;
+        }
+#endif
+}
 
 __device__ __forceinline__ void bdecode(const BOp& op, int64_t g, int64_t& o0, int64_t& o1,
                                         int64_t& o2)
@@ -85,6 +101,7 @@ __device__ __forceinline__ void bdecode(const BOp& op, int64_t g, int64_t& o0, i
             o1 += (int64_t)i * op.s1[d];
             o2 += (int64_t)i * op.s2[d];
         }
+        bcheck(op, o0, o1, o2);
         return;
     }
     for (int d = 0; d < op.nd; ++d) {
@@ -100,6 +117,7 @@ __device__ __forceinline__ void bdecode(const BOp& op, int64_t g, int64_t& o0, i
         o1 += i * op.s1[d];
         o2 += i * op.s2[d];
     }
+    bcheck(op, o0, o1, o2);
 }
 
 template <typename T>
@@ -682,6 +700,8 @@ static int fill_op(const tl_op& o, BOp& b, size_t& bytes, bool& direct)
         b.nq = P.nq;
         b.saq = P.saq;
         b.incb = o.incb;
+        b.lim[0] = debug_limit(P.out.limit[0]);
+        b.lim[1] = debug_limit(P.out.limit[1]);
         b.A = A.data;
         b.B = o.vec;
         b.C = C.data;
@@ -708,6 +728,8 @@ static int fill_op(const tl_op& o, BOp& b, size_t& bytes, bool& direct)
         b.count = P.M;
         b.nq = P.nq;
         b.saq = P.saq;
+        b.lim[0] = debug_limit(P.rows.limit[0]);
+        b.lim[1] = debug_limit(P.rows.limit[1]);
         b.J = P.J;
         b.scq = P.scq;
         b.ldb_row = P.ldb_row;
@@ -736,6 +758,7 @@ static int fill_op(const tl_op& o, BOp& b, size_t& bytes, bool& direct)
             b.s2[d] = P.sp.d[d].s[2];
         }
         b.count = P.N;
+        for (int k = 0; k < 3; ++k) b.lim[k] = debug_limit(P.sp.limit[k]);
         b.eop = o.entry_op;
         b.alpha = o.alpha;
         b.A = A.data;

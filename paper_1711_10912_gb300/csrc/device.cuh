@@ -5,10 +5,55 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cstdlib>
 
 #include "plan.h"
 
 namespace tl {
+
+// Registers a reader of one file's bounds-violation word (bounds-checked
+// builds); tl_device_status() calls every reader.
+int register_bounds_reader(int (*reader)(bool clear));
+
+#ifdef TL_CHECK_BOUNDS
+// Bounds-checked build: each file that includes this header has its own word
+// (no relocatable device code), holding 1 + the first offending offset.
+static __device__ unsigned long long g_bounds_bad = 0;
+
+__device__ __forceinline__ void bounds_record(int64_t off)
+{
+    atomicCAS(&g_bounds_bad, 0ull, 1ull + ((unsigned long long)off & 0x7fffffffffffffffull));
+}
+
+namespace {
+int bounds_read(bool clear)
+{
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bounds_bad, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return TL_ECUDA;
+    }
+    if (v && clear) {
+        const unsigned long long zero = 0;
+        cudaMemcpyToSymbol(g_bounds_bad, &zero, sizeof zero);
+    }
+    return v ? TL_EBOUNDS : TL_OK;
+}
+[[maybe_unused]] const int g_bounds_registered = register_bounds_reader(&bounds_read);
+}  // namespace
+
+// Checked builds: TL_DEBUG_SHRINK_LIMITS set in the environment halves every
+// limit handed to a kernel, so that in-range accesses are reported (and
+// skipped) -- a way to show the check works without touching memory out of
+// range.
+inline int64_t debug_limit(int64_t lim)
+{
+    static const bool shrink = std::getenv("TL_DEBUG_SHRINK_LIMITS") != nullptr;
+    return shrink && lim > 1 ? lim / 2 : lim;
+}
+#else
+inline int64_t debug_limit(int64_t lim) { return lim; }
+#endif
 
 // Collapsed iteration space as kernel parameters: dims[0] varies fastest.
 // small != 0 when every linear index fits in 31 bits, so the mapper can use
@@ -18,6 +63,7 @@ struct DevSpace {
     int small;
     int64_t n[kMaxDims];
     int64_t s[3][kMaxDims];
+    int64_t limit[3];   // see Space::limit (checked builds)
 };
 
 inline DevSpace to_dev(const Space& sp)
@@ -29,7 +75,26 @@ inline DevSpace to_dev(const Space& sp)
         for (int o = 0; o < 3; ++o) d.s[o][i] = sp.d[i].s[o];
     }
     d.small = sp.count() < (int64_t(1) << 31) ? 1 : 0;
+    for (int o = 0; o < 3; ++o) d.limit[o] = debug_limit(sp.limit[o]);
     return d;
+}
+
+// Bounds-checked builds: an offset whose addressed elements (a vector of
+// `vec0` along dim 0) fall outside the operand's limit is recorded and
+// replaced by 0; product builds compile this away.
+template <int NOPS>
+__device__ __forceinline__ void check_offsets(const DevSpace& sp, int64_t vec0, int64_t* off)
+{
+#ifdef TL_CHECK_BOUNDS
+#pragma unroll
+    for (int o = 0; o < NOPS; ++o) {
+        const int64_t last = off[o] + (vec0 - 1) * (sp.nd > 0 ? sp.s[o][0] : 0);
+        if (sp.limit[o] > 0 && (off[o] < 0 || last >= sp.limit[o])) {
+            bounds_record(off[o]);
+            off[o] = 0;
+        }
+    }
+#endif
 }
 
 // Offsets of linear index g for operands 0..NOPS-1.  dim 0 is taken in units
@@ -57,6 +122,7 @@ __device__ __forceinline__ void map_offsets(const DevSpace& sp, int64_t g, int64
 #pragma unroll
             for (int o = 0; o < NOPS; ++o) off[o] += ii * sp.s[o][d];
         }
+        check_offsets<NOPS>(sp, vec0, off);
         return;
     }
     for (int d = 0; d < sp.nd; ++d) {
@@ -73,6 +139,7 @@ __device__ __forceinline__ void map_offsets(const DevSpace& sp, int64_t g, int64
 #pragma unroll
         for (int o = 0; o < NOPS; ++o) off[o] += i * sp.s[o][d];
     }
+    check_offsets<NOPS>(sp, vec0, off);
 }
 
 template <typename T, int V> struct Vec;

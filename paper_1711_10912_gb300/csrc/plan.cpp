@@ -159,6 +159,8 @@ int plan_ttv(const Tensor& A, int64_t incb, uint32_t q, const Tensor& C, TtvPlan
     P.nq = A.n[q - 1];
     P.saq = A.w[q - 1];
     P.incb = incb;
+    P.out.limit[0] = A.span() - (P.nq - 1) * P.saq;
+    P.out.limit[1] = C.span();
     P.nout = P.out.count();
     const int es = (int)A.elem();
     const int V = 16 / es;   // elements per 16-byte vector
@@ -231,6 +233,8 @@ int plan_ttm(const Tensor& A, int64_t J, int64_t ldb_row, int64_t ldb_col, uint3
     P.saq = A.w[q - 1];
     P.J = J;
     P.scq = C.w[q - 1];
+    P.rows.limit[0] = A.span() - (P.nq - 1) * P.saq;
+    P.rows.limit[1] = C.span() - (J - 1) * P.scq;
     P.ldb_row = ldb_row;
     P.ldb_col = ldb_col;
     P.M = P.rows.count();
@@ -287,6 +291,9 @@ int plan_entrywise(int32_t op, const Tensor& A, const Tensor* B, const Tensor& C
     }
     collapse(P.sp, 2);
     P.N = P.sp.count();
+    P.sp.limit[0] = A.span();
+    P.sp.limit[1] = B ? B->span() : A.span();
+    P.sp.limit[2] = C.span();
     const int V = 16 / (int)A.elem();
     P.vec = 1;
     P.tdim = -1;

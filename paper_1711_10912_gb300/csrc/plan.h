@@ -28,6 +28,11 @@ struct Space {
     int nd = 0;
     int nops = 0;
     Dim d[kMaxDims];
+    // exclusive bound on the offset of the last element a mapped index
+    // addresses in each operand (its span less the planned extra offset along
+    // the contraction or the output column); <= 0: not set.  Checked by the
+    // mapper in builds with TL_CHECK_BOUNDS only.
+    int64_t limit[3] = {0, 0, 0};
     int64_t count() const {
         int64_t c = 1;
         for (int i = 0; i < nd; ++i) c *= d[i].n;

@@ -33,6 +33,9 @@ struct NvtxRange {
 };
 
 int device_sms();
+// TL_EBOUNDS if a bounds-checked build recorded an out-of-range mapped offset
+// since the last cleared check, else TL_OK (TL_ECUDA if a word could not be read).
+int bounds_status(bool clear);
 // Raises `func`'s dynamic shared-memory limit to `bytes` on the current
 // device, once per (device, kernel): the attribute applies to the device that
 // is current when it is set, so a process that launches on several devices

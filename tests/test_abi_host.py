@@ -44,6 +44,7 @@ def test_binding_constants_match_the_header(tl):
     assert m, "TL_TTV_NOALLOC_SCRATCH_BYTES not found in tlgb.h"
     assert tl.TL_TTV_NOALLOC_SCRATCH_BYTES == int(m.group(1)) << int(m.group(2))
     for name in ("TL_OK", "TL_EINVAL", "TL_EUNSUPPORTED", "TL_ENOMEM", "TL_ECUDA", "TL_ETIMEOUT",
+                 "TL_ECANCELED", "TL_EBOUNDS",
                  "TL_P_F64", "TL_P_F32", "TL_P_TF32", "TL_P_BF16", "TL_P_BF16X3",
                  "TL_OP_TTV", "TL_OP_TTM", "TL_OP_ENTRYWISE"):
         m = re.search(r"#define\s+%s\s+(-?\d+)" % name, src)
