@@ -60,6 +60,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 18,
                     help="outputs per ttv/ttm op in the CPU-oracle sample")
+    ap.add_argument("--profile-case", default=None,
+                    choices=["ttm_tc_x64", "sgemm_384", "batch_512", "ew_tma_96"],
+                    help="run one small case three times and exit (the workloads the ncu "
+                         "captures under profiles/ use; no JSON line)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the FP64 calls timed against the measured DFMA rate")
@@ -506,10 +510,63 @@ def reference_arm(args):
     return 0
 
 
+def profile_case(name):
+    """Runs one small case three times (a profiler captures one launch of
+    it): ttm_tc_x64 = split-BF16x3 ttm of a 512^3 FP32 tensor by a 64 x 512
+    matrix along mode 1; sgemm_384 = FP32 ttm of 384^3 by 384 x 384 along mode
+    1; batch_512 = 512 operations of the batch recipe in one persistent
+    launch (default unit choices); ew_tma_96 = the first-order + last-order
+    add of two 96^4 FP32 tensors."""
+    import torch
+    import synth
+    from paper_1711_10912_gb300 import build as tlbuild
+    import paper_1711_10912_gb300 as tl
+    tlbuild.build()
+    tl.load_library()
+    dev = torch.device("cuda", 0)
+    sh = torch.cuda.current_stream(dev).cuda_stream
+    keep = []
+    if name in ("ttm_tc_x64", "sgemm_384"):
+        e, J, prec = (512, 64, tl.TL_P_BF16X3) if name == "ttm_tc_x64" else (384, 384, tl.TL_P_F32)
+        n = (e, e, e)
+        A = synth.device_normal(torch, e ** 3, 71_000, torch.float32, dev)
+        B = synth.device_normal(torch, J * e, 71_001, torch.float32, dev)
+        C = torch.empty(e * e * J, dtype=torch.float32, device=dev)
+        DA, DC = tl.Desc(A, n), tl.Desc(C, (J, e, e))
+        fn = lambda: tl.check(tl.tl_ttm(DA, B, J, e, 1, 1, DC, prec, 0, sh))
+    elif name == "batch_512":
+        ops = []
+        for i, u in enumerate(synth.batch_units(4096)[:512]):
+            op, _, _, _, _ = _op_for_unit(tl, torch, dev, u, 10_000 + 7 * i, keep)
+            ops.append(op)
+        rc, batch = tl.tl_batch_create(ops, 0, sh)
+        tl.check(rc)
+        keep.append(batch)
+        fn = lambda: tl.check(tl.tl_batch_run(batch, sh))
+    else:
+        n = (96,) * 4
+        N = 96 ** 4
+        A = synth.device_normal(torch, N, 71_002, torch.float32, dev)
+        B = synth.device_normal(torch, N, 71_003, torch.float32, dev)
+        C = torch.empty(N, dtype=torch.float32, device=dev)
+        DA, DB, DC = tl.Desc(A, n, (1, 2, 3, 4)), tl.Desc(B, n, (4, 3, 2, 1)), tl.Desc(C, n)
+        fn = lambda: tl.check(tl.tl_entrywise(tl.TL_ADD, DA, DB, 1.0, DC, sh))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(3):
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        print(f"{name} run {i}: {e0.elapsed_time(e1):.4f} ms", flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.profile_case:
+        return profile_case(args.profile_case)
 
     import torch
     import synth
