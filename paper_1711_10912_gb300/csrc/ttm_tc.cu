@@ -133,14 +133,31 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 // UMMA shared-memory descriptor, K-major, no swizzle: 8-row x 16-byte core
 // matrices; lbo = byte distance between core matrices along K, sbo = byte
 // distance between 8-row groups.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+// Shared-memory matrix descriptor of a K-major swizzled operand: rows of
+// `row` bytes (64: 64-byte swizzle, 128: 128-byte swizzle), 8-row groups
+// `sbo` bytes apart; the leading byte offset is unused for K-major swizzled
+// layouts (set to 16 bytes).  `addr` may point inside a swizzle atom along K
+// (the k sub-steps of a stage): the swizzle is a function of the address bits,
+// and every atom starts at a multiple of its size (base offset 0).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t row, uint32_t sbo)
 {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)1 << 16;            // leading byte offset 16 (unused)
     d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;            // descriptor version for tcgen05
-    return d;                          // base offset 0, layout type 0 (no swizzle)
+    d |= (uint64_t)(row == 128 ? 2u : 4u) << 61;   // layout: 128-byte / 64-byte swizzle
+    return d;
+}
+
+// Byte offset of 16-byte chunk c of row r in a K-major swizzled operand with
+// rows of `row` bytes: the chunk index is XORed with the row's position in
+// the swizzle pattern (128-byte swizzle: r mod 8; 64-byte swizzle: (r / 2)
+// mod 4), which spreads the rows of an 8-row group over all banks.
+__host__ __device__ __forceinline__ uint32_t sw_off(uint32_t r, uint32_t c, uint32_t row)
+{
+    const uint32_t f = row == 128 ? (r & 7u) : ((r >> 1) & 3u);
+    return r * row + ((c ^ f) << 4);
 }
 
 // Instruction descriptor: D = F32, A/B format (1 = BF16, 2 = TF32), both
@@ -283,8 +300,9 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
     constexpr int kKmma = kTF32 ? 8 : 16;           // k per MMA instruction
     constexpr int kSubs = BK / kKmma;
     constexpr int kChunks = BK * (kTF32 ? 4 : 2) / 16;   // 16-byte chunks per operand row
+    constexpr uint32_t kRow = kChunks * 16;         // operand row bytes (= swizzle width)
     constexpr uint32_t kSbo = kChunks * 128;        // bytes per 8-row group
-    constexpr uint32_t kLbo = 128;
+    constexpr uint32_t kSubBytes = kKmma * (kTF32 ? 4 : 2);   // k bytes per MMA instruction
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.ns_stg; ++s) {
@@ -399,18 +417,18 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
                         for (int c = 0; c < nchunks; ++c) {
                             const uint32_t n = (c == nchunks - 1) ? (uint32_t)(a.Jp - 256 * c) : 256u;
                             const uint32_t idesc = umma_idesc(kTF32 ? 2u : 1u, BM, n);
-                            const uint32_t boff = (uint32_t)c * (256u / 8u) * kSbo + sub * 2 * kLbo;
-                            const uint32_t aoff = sub * 2 * kLbo;
+                            const uint32_t boff = (uint32_t)c * (256u / 8u) * kSbo + sub * kSubBytes;
+                            const uint32_t aoff = sub * kSubBytes;
                             const uint32_t d = dcol + 256u * c;
                             uint32_t accum = (ks > 0 || sub > 0) ? 1u : 0u;
                             const int bs = a.b_resident ? ks : op.idx;
-                            umma<kTF32>(d, umma_desc(op_a(op.idx, 0) + aoff, kLbo, kSbo),
-                                        umma_desc(op_b(bs, 0) + boff, kLbo, kSbo), idesc, accum);
+                            umma<kTF32>(d, umma_desc(op_a(op.idx, 0) + aoff, kRow, kSbo),
+                                        umma_desc(op_b(bs, 0) + boff, kRow, kSbo), idesc, accum);
                             if constexpr (kParts == 2) {
-                                umma<kTF32>(d, umma_desc(op_a(op.idx, 0) + aoff, kLbo, kSbo),
-                                            umma_desc(op_b(bs, 1) + boff, kLbo, kSbo), idesc, 1u);
-                                umma<kTF32>(d, umma_desc(op_a(op.idx, 1) + aoff, kLbo, kSbo),
-                                            umma_desc(op_b(bs, 0) + boff, kLbo, kSbo), idesc, 1u);
+                                umma<kTF32>(d, umma_desc(op_a(op.idx, 0) + aoff, kRow, kSbo),
+                                            umma_desc(op_b(bs, 1) + boff, kRow, kSbo), idesc, 1u);
+                                umma<kTF32>(d, umma_desc(op_a(op.idx, 1) + aoff, kRow, kSbo),
+                                            umma_desc(op_b(bs, 0) + boff, kRow, kSbo), idesc, 1u);
                             }
                         }
                     }
@@ -453,17 +471,16 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
                         x[4 * c + 3] = v.w;
                     }
                 }
-                const uint32_t row_off = (uint32_t)(t >> 3) * kSbo + (uint32_t)(t & 7) * 16u;
-                uint8_t* pa0 = sbase + (op_a(op.idx, 0) - base) + row_off;
+                uint8_t* pa0 = sbase + (op_a(op.idx, 0) - base);
                 if constexpr (kTF32) {
 #pragma unroll
                     for (int c = 0; c < KH / 4; ++c) {
                         uint4 v = make_uint4(to_tf32(x[4 * c]), to_tf32(x[4 * c + 1]),
                                              to_tf32(x[4 * c + 2]), to_tf32(x[4 * c + 3]));
-                        *reinterpret_cast<uint4*>(pa0 + (kh * (KH / 4) + c) * 128) = v;
+                        *reinterpret_cast<uint4*>(pa0 + sw_off(t, kh * (KH / 4) + c, kRow)) = v;
                     }
                 } else {
-                    uint8_t* pa1 = sbase + (op_a(op.idx, kParts - 1) - base) + row_off;
+                    uint8_t* pa1 = sbase + (op_a(op.idx, kParts - 1) - base);
 #pragma unroll
                     for (int c = 0; c < KH / 8; ++c) {
                         float h[8], l[8];
@@ -475,11 +492,11 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ 
                         const int oc = kh * (KH / 8) + c;
                         uint4 vh = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]),
                                               pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
-                        *reinterpret_cast<uint4*>(pa0 + oc * 128) = vh;
+                        *reinterpret_cast<uint4*>(pa0 + sw_off(t, oc, kRow)) = vh;
                         if constexpr (kParts == 2) {
                             uint4 vl = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]),
                                                   pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
-                            *reinterpret_cast<uint4*>(pa1 + oc * 128) = vl;
+                            *reinterpret_cast<uint4*>(pa1 + sw_off(t, oc, kRow)) = vl;
                         }
                     }
                 }
@@ -688,7 +705,7 @@ __global__ void ttm_tc_prep_b(const float* __restrict__ B, int64_t ldb_row, int6
     constexpr int kParts = (PREC == TL_P_BF16X3) ? 2 : 1;
     constexpr int kEl = kTF32 ? 4 : 8;                  // elements per 16-byte chunk
     constexpr int kChunks = BK / kEl;
-    constexpr uint32_t kSbo = kChunks * 128;
+    constexpr uint32_t kRow = kChunks * 16;
     const int64_t total = (int64_t)nks * Jp * kChunks;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -701,7 +718,7 @@ __global__ void ttm_tc_prep_b(const float* __restrict__ B, int64_t ldb_row, int6
             int64_t k = (int64_t)ks * BK + c * kEl + e;
             x[e] = (j < J && k < nq) ? B[j * ldb_row + k * ldb_col] : 0.f;
         }
-        const uint32_t off = (uint32_t)(j >> 3) * kSbo + (uint32_t)c * 128u + (uint32_t)(j & 7) * 16u;
+        const uint32_t off = sw_off((uint32_t)j, (uint32_t)c, kRow);
         uint8_t* p0 = img + ((size_t)ks * kParts) * part_bytes + off;
         if constexpr (kTF32) {
             *reinterpret_cast<uint4*>(p0) =
