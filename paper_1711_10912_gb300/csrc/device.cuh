@@ -97,6 +97,25 @@ __device__ __forceinline__ void check_offsets(const DevSpace& sp, int64_t vec0, 
 #endif
 }
 
+// Bounds-checked builds: operand o's access of `vec` contiguous elements at
+// `off` (kernels that compute their own offsets) is checked against the
+// operand's limit, recorded and redirected to 0 when outside; product builds
+// return `off` unchanged.
+__device__ __forceinline__ int64_t checked_off(const DevSpace& sp, int o, int64_t off, int vec)
+{
+#ifdef TL_CHECK_BOUNDS
+    if (sp.limit[o] > 0 && (off < 0 || off + vec - 1 >= sp.limit[o])) {
+        bounds_record(off);
+        return 0;
+    }
+#else
+    (void)sp;
+    (void)o;
+    (void)vec;
+#endif
+    return off;
+}
+
 // Offsets of linear index g for operands 0..NOPS-1.  dim 0 is taken in units
 // of `vec0` elements (g counts vectors along dim 0); the last dim needs no
 // division because g is already below its extent.
@@ -138,6 +157,83 @@ __device__ __forceinline__ void map_offsets(const DevSpace& sp, int64_t g, int64
         if (d == 0) i *= vec0;
 #pragma unroll
         for (int o = 0; o < NOPS; ++o) off[o] += i * sp.s[o][d];
+    }
+    check_offsets<NOPS>(sp, vec0, off);
+}
+
+// Quotient of a 32-bit index by an invariant divisor (FastDiv, plan.h).
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv& f)
+{
+    const uint32_t t = __umulhi(f.mul, n);
+    return (t + ((n - t) >> f.sh1)) >> f.sh2;
+}
+
+// Division tables of a collapsed space whose linear indices fit in 31 bits
+// (DevSpace::small): fd[d] divides by dim d's extent, dim 0 counted in
+// vectors of `vec0` elements.
+struct DevDiv {
+    FastDiv fd[kMaxDims];
+    uint32_t ext[kMaxDims];
+};
+
+inline DevDiv make_devdiv(const Space& sp, int64_t vec0)
+{
+    DevDiv v{};
+    for (int d = 0; d < sp.nd; ++d) {
+        const int64_t ext = d == 0 ? sp.d[0].n / vec0 : sp.d[d].n;
+        v.ext[d] = (uint32_t)(ext > 0 && ext < (int64_t(1) << 32) ? ext : 1);
+        v.fd[d] = make_fastdiv(v.ext[d]);
+    }
+    return v;
+}
+
+// map_offsets with multiply-high division for spaces with 31-bit indices;
+// others take the 64-bit path of map_offsets.
+template <int NOPS>
+__device__ __forceinline__ void map_offsets_fast(const DevSpace& sp, const DevDiv& dv, int64_t g,
+                                                 int64_t vec0, int64_t* off)
+{
+    if (!sp.small) {
+        map_offsets<NOPS>(sp, g, vec0, off);
+        return;
+    }
+#pragma unroll
+    for (int o = 0; o < NOPS; ++o) off[o] = 0;
+    uint32_t r = (uint32_t)g;
+    for (int d = 0; d < sp.nd; ++d) {
+        uint32_t i = r;
+        if (d < sp.nd - 1) {
+            const uint32_t qd = fast_div(r, dv.fd[d]);
+            i = r - qd * dv.ext[d];
+            r = qd;
+        }
+        const int64_t ii = d == 0 ? (int64_t)i * vec0 : (int64_t)i;
+#pragma unroll
+        for (int o = 0; o < NOPS; ++o) off[o] += ii * sp.s[o][d];
+    }
+    check_offsets<NOPS>(sp, vec0, off);
+}
+
+// map_offsets_fast for a space of exactly ND dims with 31-bit indices: the
+// decode unrolls and reads its tables at fixed offsets.
+template <int ND, int NOPS>
+__device__ __forceinline__ void map_offsets_nd(const DevSpace& sp, const DevDiv& dv, int64_t g,
+                                               int64_t vec0, int64_t* off)
+{
+#pragma unroll
+    for (int o = 0; o < NOPS; ++o) off[o] = 0;
+    uint32_t r = (uint32_t)g;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        uint32_t i = r;
+        if (d < ND - 1) {
+            const uint32_t qd = fast_div(r, dv.fd[d]);
+            i = r - qd * dv.ext[d];
+            r = qd;
+        }
+        const int64_t ii = d == 0 ? (int64_t)i * vec0 : (int64_t)i;
+#pragma unroll
+        for (int o = 0; o < NOPS; ++o) off[o] += ii * sp.s[o][d];
     }
     check_offsets<NOPS>(sp, vec0, off);
 }

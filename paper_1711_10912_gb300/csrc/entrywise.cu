@@ -8,16 +8,21 @@
 //   ew_flat     A, B and C share one contiguous layout: a flat stream with
 //               16-byte vectors.
 //   ew_tile     an input's fastest dim t differs from C's fastest dim 0: a
-//               32 x 32 tile over dims (0, t) is read along t (coalesced for
-//               that input), transposed in shared memory and written along
-//               dim 0 (coalesced for C); an input already contiguous along
-//               dim 0 is read directly in the write phase.
+//               tile over dims (0, t) is read along t (coalesced for that
+//               input), transposed in shared memory and written along dim 0
+//               (coalesced for C); an input already contiguous along dim 0
+//               is read directly.  16-byte vectors and one 64 x 64 (FP32) or
+//               32 x 32 (FP64) tile per CTA when extents and strides allow,
+//               else 32 x 32 element tiles.
 //   ew_rows     every operand is contiguous along dim 0 but the other dims
 //               are ordered differently: one offset decode per 16-byte vector.
 //   ew_generic  anything else: each element's offsets come from the mapper.
-// FP32 cases of ew_tile and ew_rows that a tensor map can describe run on the
-// TMA-staged kernel of ew_tma.cu instead.
+// FP32 tiles that the vector kernel cannot take (a ragged extent in a padded
+// view) but a tensor map can describe run on the TMA-staged kernel of
+// ew_tma.cu instead.
 #include <cuda_runtime.h>
+
+#include <cstdint>
 
 #include "device.cuh"
 #include "kernels.h"
@@ -35,9 +40,64 @@ struct EwArgs {
     int tdim;
     int64_t N;
     DevSpace sp;        // operands 0 = A, 1 = B, 2 = C
+    DevDiv dv;          // ew_rows: division by the extents (dim 0 in vectors)
+    // tile kernels: the tile index is (tile along dim 0, tile along t, batch
+    // dims); idx32 when it fits in 31 bits (multiply-high division)
+    int idx32;
+    uint32_t ntile0, ntile1;
+    FastDiv ft0, ft1;
+    int nb;
+    uint32_t bext[kMaxDims];
+    FastDiv fb[kMaxDims];
+    int64_t bs[3][kMaxDims];   // operands' strides along the batch dims
 };
 
 constexpr int kThreads = 256;
+
+// Decodes tile index blk into its tile coordinates along dim 0 and t and the
+// operands' offsets of its batch index.  NB >= 0 is the number of batch dims
+// known at compile time (unrolled, the division tables read at fixed
+// offsets); NB < 0 reads it from the arguments.
+template <int NB>
+__device__ __forceinline__ void tile_decode(const EwArgs& a, int64_t blk, int64_t& bt0,
+                                            int64_t& bt1, int64_t* base)
+{
+    constexpr int KMAX = NB >= 0 ? NB : kMaxDims;
+    const int nb = NB >= 0 ? NB : a.nb;
+    base[0] = base[1] = base[2] = 0;
+    if (a.idx32) {
+        uint32_t r = (uint32_t)blk;
+        uint32_t q = fast_div(r, a.ft0);
+        bt0 = r - q * a.ntile0;
+        r = q;
+        q = fast_div(r, a.ft1);
+        bt1 = r - q * a.ntile1;
+        r = q;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            if (k >= nb) break;
+            uint32_t i = r;
+            if (k < nb - 1) {
+                q = fast_div(r, a.fb[k]);
+                i = r - q * a.bext[k];
+                r = q;
+            }
+#pragma unroll
+            for (int o = 0; o < 3; ++o) base[o] += (int64_t)i * a.bs[o][k];
+        }
+        return;
+    }
+    bt0 = blk % a.ntile0;
+    int64_t g = blk / a.ntile0;
+    bt1 = g % a.ntile1;
+    g /= a.ntile1;
+    for (int k = 0; k < nb; ++k) {
+        const int64_t i = g % a.bext[k];
+        g /= a.bext[k];
+#pragma unroll
+        for (int o = 0; o < 3; ++o) base[o] += i * a.bs[o][k];
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ T apply(int op, T a, T b, T alpha)
@@ -52,7 +112,13 @@ __device__ __forceinline__ T apply(int op, T a, T b, T alpha)
     }
 }
 
-template <typename T, int VEC>
+// Flat stream: U vectors of VEC elements per thread (kThreads apart, so a
+// warp's accesses stay contiguous), all loads issued before the stores, and a
+// grid of one such chunk per thread (grid-stride only beyond the largest
+// grid).  Many short-lived CTAs keep more loads in flight than a persistent
+// grid: an FP32 add of 1 GiB operands ran at 7.1 TB/s this way against 6.65
+// with a grid of 8 CTAs per SM looping over the stream.
+template <typename T, int VEC, int U>
 __global__ void __launch_bounds__(kThreads) ew_flat_kernel(const EwArgs a)
 {
     const T* __restrict__ A = static_cast<const T*>(a.A);
@@ -61,37 +127,32 @@ __global__ void __launch_bounds__(kThreads) ew_flat_kernel(const EwArgs a)
     const T alpha = (T)a.alpha;
     const bool unary = (a.op == TL_COPY || a.op == TL_SCALE);
     const int64_t nvec = a.N / VEC;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    // two vectors per thread per iteration keep more loads in flight
-    for (; i + stride < nvec; i += 2 * stride) {
-        T x0[VEC], y0[VEC], x1[VEC], y1[VEC], r0[VEC], r1[VEC];
-        vload_stream<T, VEC>(A + i * VEC, x0);
-        vload_stream<T, VEC>(A + (i + stride) * VEC, x1);
-        if (!unary) {
-            vload_stream<T, VEC>(B + i * VEC, y0);
-            vload_stream<T, VEC>(B + (i + stride) * VEC, y1);
+    const int64_t step = (int64_t)gridDim.x * kThreads * U;
+    for (int64_t g0 = (int64_t)blockIdx.x * kThreads * U + threadIdx.x; g0 < nvec; g0 += step) {
+        T x[U][VEC], y[U][VEC];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t g = g0 + (int64_t)u * kThreads;
+            if (g < nvec) {
+                vload_stream<T, VEC>(A + g * VEC, x[u]);
+                if (!unary) vload_stream<T, VEC>(B + g * VEC, y[u]);
+            }
         }
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            r0[v] = apply<T>(a.op, x0[v], unary ? T(0) : y0[v], alpha);
-            r1[v] = apply<T>(a.op, x1[v], unary ? T(0) : y1[v], alpha);
-        }
-        vstore<T, VEC>(C + i * VEC, r0);
-        vstore<T, VEC>(C + (i + stride) * VEC, r1);
-    }
-    for (; i < nvec; i += stride) {
-        T x[VEC], y[VEC], r[VEC];
-        vload_stream<T, VEC>(A + i * VEC, x);
-        if (!unary) vload_stream<T, VEC>(B + i * VEC, y);
+        for (int u = 0; u < U; ++u) {
+            const int64_t g = g0 + (int64_t)u * kThreads;
+            if (g < nvec) {
+                T r[VEC];
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) r[v] = apply<T>(a.op, x[v], unary ? T(0) : y[v], alpha);
-        vstore<T, VEC>(C + i * VEC, r);
+                for (int v = 0; v < VEC; ++v) r[v] = apply<T>(a.op, x[u][v], unary ? T(0) : y[u][v], alpha);
+                vstore<T, VEC>(C + g * VEC, r);
+            }
+        }
     }
-    // scalar tail
-    const int64_t tail0 = nvec * VEC;
-    for (int64_t e = tail0 + (int64_t)blockIdx.x * kThreads + threadIdx.x; e < a.N; e += stride) {
-        C[e] = apply<T>(a.op, A[e], unary ? T(0) : B[e], alpha);
+    // scalar tail (fewer than VEC elements)
+    if (blockIdx.x == 0) {
+        const int64_t e = nvec * VEC + threadIdx.x;
+        if (e < a.N) C[e] = apply<T>(a.op, A[e], unary ? T(0) : B[e], alpha);
     }
 }
 
@@ -114,12 +175,16 @@ __global__ void __launch_bounds__(kThreads) ew_generic_kernel(const EwArgs a)
 }
 
 // All operands unit-stride along dim 0 but laid out differently in the other
-// dims: one offset decode per 16-byte vector along dim 0, vector loads and
-// stores (dim 0's extent and every other stride are multiples of VEC).  Each
-// thread issues the loads of U vectors before their stores, so a resident
-// SM keeps enough bytes in flight to cover the HBM latency.
-template <typename T, int VEC, int U>
-__global__ void __launch_bounds__(kThreads, 4) ew_rows_kernel(const EwArgs a)
+// dims: one offset decode per 16-byte vector along dim 0 (multiply-high
+// division), vector loads and stores (dim 0's extent and every other stride
+// are multiples of VEC).  Each thread issues the loads of its U vectors
+// (kThreads apart) before their stores, one such chunk per thread as in
+// ew_flat.  ND > 0 is the collapsed dim count, known at compile time so the
+// decode unrolls: on permuted rows of 128^4 FP32 tensors that took the add
+// from 6.0 to 6.9 TB/s and the copy from 4.4 to 5.9 (the decode's latency
+// sits in front of every load).
+template <typename T, int VEC, int U, int ND>
+__global__ void __launch_bounds__(kThreads) ew_rows_kernel(const EwArgs a)
 {
     const T* __restrict__ A = static_cast<const T*>(a.A);
     const T* __restrict__ B = static_cast<const T*>(a.B);
@@ -127,36 +192,31 @@ __global__ void __launch_bounds__(kThreads, 4) ew_rows_kernel(const EwArgs a)
     const T alpha = (T)a.alpha;
     const bool unary = (a.op == TL_COPY || a.op == TL_SCALE);
     const int64_t nvec = a.N / VEC;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    for (; g + (U - 1) * stride < nvec; g += U * stride) {
+    const int64_t step = (int64_t)gridDim.x * kThreads * U;
+    for (int64_t g0 = (int64_t)blockIdx.x * kThreads * U + threadIdx.x; g0 < nvec; g0 += step) {
         int64_t off[U][3];
         T x[U][VEC], y[U][VEC];
 #pragma unroll
-        for (int u = 0; u < U; ++u) map_offsets<3>(a.sp, g + u * stride, VEC, off[u]);
-#pragma unroll
         for (int u = 0; u < U; ++u) {
-            vload_stream<T, VEC>(A + off[u][0], x[u]);
-            if (!unary) vload_stream<T, VEC>(B + off[u][1], y[u]);
+            const int64_t g = g0 + (int64_t)u * kThreads;
+            if (g < nvec) {
+                if constexpr (ND > 0) map_offsets_nd<ND, 3>(a.sp, a.dv, g, VEC, off[u]);
+                else map_offsets_fast<3>(a.sp, a.dv, g, VEC, off[u]);
+                vload_stream<T, VEC>(A + off[u][0], x[u]);
+                if (!unary) vload_stream<T, VEC>(B + off[u][1], y[u]);
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            T r[VEC];
+            const int64_t g = g0 + (int64_t)u * kThreads;
+            if (g < nvec) {
+                T r[VEC];
 #pragma unroll
-            for (int v = 0; v < VEC; ++v)
-                r[v] = apply<T>(a.op, x[u][v], unary ? T(0) : y[u][v], alpha);
-            vstore<T, VEC>(C + off[u][2], r);
+                for (int v = 0; v < VEC; ++v)
+                    r[v] = apply<T>(a.op, x[u][v], unary ? T(0) : y[u][v], alpha);
+                vstore<T, VEC>(C + off[u][2], r);
+            }
         }
-    }
-    for (; g < nvec; g += stride) {
-        int64_t off[3];
-        map_offsets<3>(a.sp, g, VEC, off);
-        T x[VEC], y[VEC], r[VEC];
-        vload_stream<T, VEC>(A + off[0], x);
-        if (!unary) vload_stream<T, VEC>(B + off[1], y);
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) r[v] = apply<T>(a.op, x[v], unary ? T(0) : y[v], alpha);
-        vstore<T, VEC>(C + off[2], r);
     }
 }
 
@@ -207,8 +267,12 @@ __global__ void __launch_bounds__(kThreads) ew_tile_kernel(const EwArgs a, int64
             for (int r = 0; r < kTile; r += 8) {
                 int64_t i0 = i0b + ty + r, it = itb + tx;
                 if (i0 < n0 && it < nt) {
-                    if (stageA) tA[ty + r][tx] = __ldcs(A + base[0] + i0 * a.sp.s[0][0] + it * a.sp.s[0][t]);
-                    if (stageB) tB[ty + r][tx] = __ldcs(B + base[1] + i0 * a.sp.s[1][0] + it * a.sp.s[1][t]);
+                    if (stageA)
+                        tA[ty + r][tx] = __ldcs(A + checked_off(a.sp, 0, base[0] + i0 * a.sp.s[0][0] +
+                                                                     it * a.sp.s[0][t], 1));
+                    if (stageB)
+                        tB[ty + r][tx] = __ldcs(B + checked_off(a.sp, 1, base[1] + i0 * a.sp.s[1][0] +
+                                                                     it * a.sp.s[1][t], 1));
                 }
             }
         }
@@ -219,106 +283,161 @@ __global__ void __launch_bounds__(kThreads) ew_tile_kernel(const EwArgs a, int64
             int64_t i0 = i0b + tx, it = itb + ty + r;
             if (i0 < n0 && it < nt) {
                 T x = stageA ? tA[tx][ty + r]
-                             : __ldcs(A + base[0] + i0 * a.sp.s[0][0] + it * a.sp.s[0][t]);
+                             : __ldcs(A + checked_off(a.sp, 0, base[0] + i0 * a.sp.s[0][0] +
+                                                                   it * a.sp.s[0][t], 1));
                 T y = T(0);
                 if (!unary)
                     y = stageB ? tB[tx][ty + r]
-                               : __ldcs(B + base[1] + i0 * a.sp.s[1][0] + it * a.sp.s[1][t]);
-                C[base[2] + i0 * a.sp.s[2][0] + it * a.sp.s[2][t]] = apply<T>(a.op, x, y, alpha);
+                               : __ldcs(B + checked_off(a.sp, 1, base[1] + i0 * a.sp.s[1][0] +
+                                                                     it * a.sp.s[1][t], 1));
+                C[checked_off(a.sp, 2, base[2] + i0 * a.sp.s[2][0] + it * a.sp.s[2][t], 1)] =
+                    apply<T>(a.op, x, y, alpha);
             }
         }
     }
 }
 
-// Vectorised variant of the tile kernel: TILE x TILE elements (64 for FP32,
-// 32 for FP64), 16-byte global accesses along each operand's unit-stride
-// dim, and every global load of a tile issued before the shared-memory
-// hand-off.  Chosen by the planner when extents and strides allow 16-byte
-// vectors for all three operands.
-template <typename T>
-__global__ void __launch_bounds__(kThreads, 4) ew_tile_vec_kernel(const EwArgs a, int64_t tiles0,
-                                                               int64_t tiles1, int64_t batch)
+// Vectorised tile kernel: TILE x TILE elements over dims (0, t), TILE = 64
+// for FP32 and 32 for FP64 (256-byte rows either way), one tile per CTA
+// (a grid-stride loop only when the tiles outnumber the largest grid).
+// Chosen when extents and strides allow 16-byte vectors for all operands.
+// SA / SB say which inputs are staged (unit stride along t); UN marks the
+// unary operations (COPY, SCALE: B absent); NB is the number of batch dims
+// when known at compile time (tile_decode).  Phase 1 reads a staged input as
+// 16-byte vectors along t into a padded [dim 0][t] shared tile and a direct
+// input (unit stride along dim 0) as 16-byte vectors along dim 0 into
+// registers, in the positions phase 2 writes.  Phase 2 writes C along dim 0:
+// eight lanes cover 128 contiguous bytes and a warp four t-rows, so the
+// staged values it reads from shared memory (column t, rows x..x+VEC-1) fall
+// in distinct banks.  Small CTAs, one tile each, keep many tiles' loads in
+// flight per SM; binary operations issue every global load of the tile
+// before any shared-memory store (up to 4 CTAs per SM), unary ones store each
+// load as it arrives (6 CTAs per SM).  On 128^4 FP32 tensors, every
+// transposed layout pair: adds 6.6-7.1 TB/s, copies 6.3-7.0; the TMA-staged
+// kernel ran them at 5.0-6.8 (its boxes of 128 rows 8 MB apart are the slow
+// case), and storing each load at once, or capping binary operations at 6
+// CTAs per SM, left the add of the reversed layouts at 5.3-6.0.
+template <typename T, bool SA, bool SB, bool UN, int NB>
+__global__ void __launch_bounds__(kThreads, UN ? 6 : 4) ew_tile_vec_kernel(const EwArgs a, int64_t total)
 {
     constexpr int VEC = 16 / sizeof(T);
     constexpr int TILE = 16 * VEC;
-    constexpr int CH = TILE / VEC;          // vectors per tile row (16)
-    constexpr int RPP = kThreads / CH;      // tile rows per pass (16)
-    constexpr int NP = TILE / RPP;          // passes
-    __shared__ T tA[TILE][TILE + 1];
-    __shared__ T tB[TILE][TILE + 1];
+    constexpr int LD = TILE + 1;                       // padded shared row
+    constexpr int NV = TILE * TILE / VEC / kThreads;   // vectors per thread and operand
+    static_assert(NV * VEC * kThreads == TILE * TILE, "tile / block mismatch");
+    extern __shared__ __align__(16) unsigned char ew_smem[];
+    T* const tA = reinterpret_cast<T*>(ew_smem);
+    T* const tB = tA + (SA ? TILE * LD : 0);
     const T* __restrict__ A = static_cast<const T*>(a.A);
     const T* __restrict__ B = static_cast<const T*>(a.B);
     T* __restrict__ C = static_cast<T*>(a.C);
     const T alpha = (T)a.alpha;
-    const bool unary = (a.op == TL_COPY || a.op == TL_SCALE);
     const int t = a.tdim;
-    const int ch = threadIdx.x % CH, rr = threadIdx.x / CH;
     const int64_t n0 = a.sp.n[0], nt = a.sp.n[t];
-    const bool stageA = a.sp.s[0][t] < a.sp.s[0][0];
-    const bool stageB = !unary && a.sp.s[1][t] < a.sp.s[1][0];
-    const int64_t total = tiles0 * tiles1 * batch;
+    const int64_t sA0 = a.sp.s[0][0], sAt = a.sp.s[0][t], sB0 = a.sp.s[1][0], sBt = a.sp.s[1][t];
+    const int64_t sCt = a.sp.s[2][t];
     for (int64_t blk = blockIdx.x; blk < total; blk += gridDim.x) {
-        int64_t bt0 = blk % tiles0;
-        int64_t rest = blk / tiles0;
-        int64_t bt1 = rest % tiles1;
-        int64_t bz = rest / tiles1;
-        int64_t base[3] = {0, 0, 0};
-        {
-            int64_t g = bz;
-            for (int d = 1; d < a.sp.nd; ++d) {
-                if (d == t) continue;
-                int64_t i = g % a.sp.n[d];
-                g /= a.sp.n[d];
-#pragma unroll
-                for (int o = 0; o < 3; ++o) base[o] += i * a.sp.s[o][d];
-            }
-        }
+        int64_t bt0, bt1, base[3];
+        tile_decode<NB>(a, blk, bt0, bt1, base);
         const int64_t i0b = bt0 * TILE, itb = bt1 * TILE;
-        T xa[NP][VEC], xb[NP][VEC];
-        __syncthreads();
+        T xa[SA ? 1 : NV][VEC], xb[(SB || UN) ? 1 : NV][VEC];
+        if constexpr (UN) {
+            // unary (one staged input): each load is followed by its
+            // shared-memory store
 #pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            // staged operands: vectors along t; direct operands: along dim 0
-            const int64_t i0s = i0b + rr + p * RPP, its = itb + ch * VEC;
-            const int64_t i0d = i0b + ch * VEC, itd = itb + rr + p * RPP;
-            if (stageA) {
+            for (int k = 0; k < NV; ++k) {
+                const int v = threadIdx.x + kThreads * k;
+                const int ts = (v % (TILE / VEC)) * VEC, xs = v / (TILE / VEC);
+                const int64_t i0s = i0b + xs, its = itb + ts;
                 if (i0s < n0 && its < nt) {
                     T x[VEC];
-                    vload_stream<T, VEC>(A + base[0] + i0s * a.sp.s[0][0] + its, x);
+                    vload_stream<T, VEC>(A + checked_off(a.sp, 0, base[0] + i0s * sA0 + its, VEC), x);
 #pragma unroll
-                    for (int e = 0; e < VEC; ++e) tA[ch * VEC + e][rr + p * RPP] = x[e];
+                    for (int e = 0; e < VEC; ++e) tA[xs * LD + ts + e] = x[e];
                 }
-            } else if (i0d < n0 && itd < nt) {
-                vload_stream<T, VEC>(A + base[0] + i0d + itd * a.sp.s[0][t], xa[p]);
             }
-            if (!unary) {
-                if (stageB) {
-                    if (i0s < n0 && its < nt) {
-                        T x[VEC];
-                        vload_stream<T, VEC>(B + base[1] + i0s * a.sp.s[1][0] + its, x);
+            __syncthreads();
+        } else {
+            T ya[SA ? NV : 1][VEC], yb[SB ? NV : 1][VEC];   // staged values on their way to smem
+            bool oks[NV];
+            // every global load of the tile first, then the shared-memory stores
 #pragma unroll
-                        for (int e = 0; e < VEC; ++e) tB[ch * VEC + e][rr + p * RPP] = x[e];
+            for (int k = 0; k < NV; ++k) {
+                const int v = threadIdx.x + kThreads * k;
+                // staged order: TILE / VEC vectors along t per dim-0 row
+                const int ts = (v % (TILE / VEC)) * VEC, xs = v / (TILE / VEC);
+                // write order: 8 vectors along dim 0, 4 t-rows, 2 halves of dim 0
+                const int xd = ((v >> 5) & 1) * 8 * VEC + (v & 7) * VEC;
+                const int td = (v >> 6) * 4 + ((v >> 3) & 3);
+                const int64_t i0s = i0b + xs, its = itb + ts, i0d = i0b + xd, itd = itb + td;
+                oks[k] = i0s < n0 && its < nt;
+                const bool okd = i0d < n0 && itd < nt;
+                if constexpr (SA) {
+                    if (oks[k])
+                        vload_stream<T, VEC>(A + checked_off(a.sp, 0, base[0] + i0s * sA0 + its, VEC),
+                                             ya[k]);
+                } else if (okd) {
+                    vload_stream<T, VEC>(A + checked_off(a.sp, 0, base[0] + i0d + itd * sAt, VEC),
+                                         xa[k]);
+                }
+                if constexpr (SB) {
+                    if (oks[k])
+                        vload_stream<T, VEC>(B + checked_off(a.sp, 1, base[1] + i0s * sB0 + its, VEC),
+                                             yb[k]);
+                } else if constexpr (!UN) {
+                    if (okd)
+                        vload_stream<T, VEC>(B + checked_off(a.sp, 1, base[1] + i0d + itd * sBt, VEC),
+                                             xb[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                const int v = threadIdx.x + kThreads * k;
+                const int ts = (v % (TILE / VEC)) * VEC, xs = v / (TILE / VEC);
+                if (oks[k]) {
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        if constexpr (SA) tA[xs * LD + ts + e] = ya[k][e];
+                        if constexpr (SB) tB[xs * LD + ts + e] = yb[k][e];
                     }
-                } else if (i0d < n0 && itd < nt) {
-                    vload_stream<T, VEC>(B + base[1] + i0d + itd * a.sp.s[1][t], xb[p]);
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
 #pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            const int64_t i0 = i0b + ch * VEC, it = itb + rr + p * RPP;
+        for (int k = 0; k < NV; ++k) {
+            const int v = threadIdx.x + kThreads * k;
+            const int xd = ((v >> 5) & 1) * 8 * VEC + (v & 7) * VEC;
+            const int td = (v >> 6) * 4 + ((v >> 3) & 3);
+            const int64_t i0 = i0b + xd, it = itb + td;
             if (i0 < n0 && it < nt) {
                 T r[VEC];
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) {
-                    T x = stageA ? tA[rr + p * RPP][ch * VEC + e] : xa[p][e];
-                    T y = unary ? T(0) : (stageB ? tB[rr + p * RPP][ch * VEC + e] : xb[p][e]);
+                    const T x = SA ? tA[(xd + e) * LD + td] : xa[SA ? 0 : k][e];
+                    T y = T(0);
+                    if constexpr (SB) y = tB[(xd + e) * LD + td];
+                    else if constexpr (!UN) y = xb[k][e];
                     r[e] = apply<T>(a.op, x, y, alpha);
                 }
-                vstore<T, VEC>(C + base[2] + i0 + it * a.sp.s[2][t], r);
+                vstore<T, VEC>(C + checked_off(a.sp, 2, base[2] + i0 + it * sCt, VEC), r);
             }
         }
+        __syncthreads();   // the next tile (grid-stride case) reuses the shared tiles
+    }
+}
+
+// Launches the vector tile kernel for staging kind vkind (0 unary, 1 both
+// inputs staged, 2 A staged, 3 B staged) and NB batch dims.
+template <typename T, int NB>
+void launch_tile_vec(int vkind, int grid, size_t smem, cudaStream_t st, const EwArgs& a,
+                     int64_t total)
+{
+    switch (vkind) {
+    case 0: ew_tile_vec_kernel<T, true, false, true, NB><<<grid, kThreads, smem, st>>>(a, total); break;
+    case 1: ew_tile_vec_kernel<T, true, true, false, NB><<<grid, kThreads, smem, st>>>(a, total); break;
+    case 2: ew_tile_vec_kernel<T, true, false, false, NB><<<grid, kThreads, smem, st>>>(a, total); break;
+    default: ew_tile_vec_kernel<T, false, true, false, NB><<<grid, kThreads, smem, st>>>(a, total); break;
     }
 }
 
@@ -344,22 +463,68 @@ int launch_typed(const EwPlan& P, const void* A, const void* B, double alpha, vo
     a.N = P.N;
     a.sp = to_dev(P.sp);
     constexpr int V = 16 / sizeof(T);
+    constexpr int U = 2;   // vectors per thread (flat, rows)
+    auto chunk_grid = [](int64_t nvec) {
+        const int64_t g = (nvec + (int64_t)kThreads * U - 1) / ((int64_t)kThreads * U);
+        return (int)(g < 1 ? 1 : (g < INT32_MAX ? g : INT32_MAX));
+    };
     if (P.kernel == K_EW_FLAT) {
-        int grid = grid_for((P.N / P.vec + 1) / 2, num_sms);
-        if (P.vec == V) ew_flat_kernel<T, V><<<grid, kThreads, 0, st>>>(a);
-        else ew_flat_kernel<T, 1><<<grid, kThreads, 0, st>>>(a);
+        if (P.vec == V) ew_flat_kernel<T, V, U><<<chunk_grid(P.N / V), kThreads, 0, st>>>(a);
+        else ew_flat_kernel<T, 1, U><<<chunk_grid(P.N), kThreads, 0, st>>>(a);
     } else if (P.kernel == K_EW_TILE) {
         const int tile = P.vec > 1 ? 16 * V : kTile;
         int64_t tiles0 = (P.sp.d[0].n + tile - 1) / tile;
         int64_t tiles1 = (P.sp.d[P.tdim].n + tile - 1) / tile;
         int64_t batch = P.N / (P.sp.d[0].n * P.sp.d[P.tdim].n);
         int64_t total = tiles0 * tiles1 * batch;
-        int64_t cap = (int64_t)num_sms * 8;
-        int grid = (int)(total < cap ? total : cap);
-        if (P.vec > 1) ew_tile_vec_kernel<T><<<grid, kThreads, 0, st>>>(a, tiles0, tiles1, batch);
-        else ew_tile_kernel<T><<<grid, kThreads, 0, st>>>(a, tiles0, tiles1, batch);
+        const bool unary = P.op == TL_COPY || P.op == TL_SCALE;
+        const bool sa = P.sp.d[P.tdim].s[0] < P.sp.d[0].s[0];
+        const bool sb = !unary && P.sp.d[P.tdim].s[1] < P.sp.d[0].s[1];
+        if (P.vec > 1 && (sa || sb)) {
+            // tile decode tables: tiles along dim 0 and t, then the batch dims
+            a.ntile0 = (uint32_t)tiles0;
+            a.ntile1 = (uint32_t)tiles1;
+            a.idx32 = total < (int64_t(1) << 31) ? 1 : 0;
+            a.ft0 = make_fastdiv(a.idx32 ? a.ntile0 : 1);
+            a.ft1 = make_fastdiv(a.idx32 ? a.ntile1 : 1);
+            a.nb = 0;
+            for (int d = 1; d < P.sp.nd; ++d) {
+                if (d == P.tdim) continue;
+                a.bext[a.nb] = (uint32_t)P.sp.d[d].n;
+                a.fb[a.nb] = make_fastdiv(a.idx32 ? a.bext[a.nb] : 1);
+                for (int o = 0; o < 3; ++o) a.bs[o][a.nb] = P.sp.d[d].s[o];
+                ++a.nb;
+            }
+            if (!a.idx32 && (tiles0 >= (int64_t(1) << 32) || tiles1 >= (int64_t(1) << 32)))
+                return TL_EUNSUPPORTED;
+            // one tile per CTA; an input is staged when dim t is its faster
+            // dim of the two (the planner's vector conditions make it unit
+            // stride there)
+            const int grid = (int)(total < INT32_MAX ? total : INT32_MAX);
+            const size_t smem = (size_t)((sa ? 1 : 0) + (sb ? 1 : 0)) * tile * (tile + 1) * sizeof(T);
+            const int vkind = unary ? 0 : (sa && sb) ? 1 : sa ? 2 : 3;
+            switch (a.idx32 ? a.nb : -1) {
+            case 0: launch_tile_vec<T, 0>(vkind, grid, smem, st, a, total); break;
+            case 1: launch_tile_vec<T, 1>(vkind, grid, smem, st, a, total); break;
+            case 2: launch_tile_vec<T, 2>(vkind, grid, smem, st, a, total); break;
+            case 3: launch_tile_vec<T, 3>(vkind, grid, smem, st, a, total); break;
+            default: launch_tile_vec<T, -1>(vkind, grid, smem, st, a, total); break;
+            }
+        } else {
+            const int64_t cap = (int64_t)num_sms * 8;
+            const int grid = (int)(total < cap ? total : cap);
+            ew_tile_kernel<T><<<grid, kThreads, 0, st>>>(a, tiles0, tiles1, batch);
+        }
     } else if (P.kernel == K_EW_ROWS) {
-        ew_rows_kernel<T, V, 2><<<grid_for((P.N / V + 1) / 2, num_sms), kThreads, 0, st>>>(a);
+        a.dv = make_devdiv(P.sp, V);
+        const int grid = chunk_grid(P.N / V);
+        switch (a.sp.small ? P.sp.nd : 0) {
+        case 2: ew_rows_kernel<T, V, U, 2><<<grid, kThreads, 0, st>>>(a); break;
+        case 3: ew_rows_kernel<T, V, U, 3><<<grid, kThreads, 0, st>>>(a); break;
+        case 4: ew_rows_kernel<T, V, U, 4><<<grid, kThreads, 0, st>>>(a); break;
+        case 5: ew_rows_kernel<T, V, U, 5><<<grid, kThreads, 0, st>>>(a); break;
+        default: ew_rows_kernel<T, V, U, 0><<<grid, kThreads, 0, st>>>(a); break;
+        }
     } else {
         ew_generic_kernel<T><<<grid_for(P.N, num_sms), kThreads, 0, st>>>(a);
     }

@@ -359,11 +359,15 @@ int plan_entrywise(int32_t op, const Tensor& A, const Tensor* B, const Tensor& C
             return TL_OK;
         }
     }
-    // FP32 tiles and permuted rows go through TMA-staged 32 x 32 tiles when
-    // every input is unit-stride along dim 0 or along the tiled dim t, C along
-    // dim 0, there are at most 5 dims (the tensor-map rank), every other
-    // stride is a multiple of 16 bytes and the bases are 16-byte aligned.
-    if (A.dtype == TL_F32 && (P.kernel == K_EW_TILE || P.kernel == K_EW_ROWS) && P.sp.nd >= 2 &&
+    // FP32 tiles whose extents rule out the 16-byte vector tile kernel (a
+    // ragged extent in a padded view) go through TMA-staged 32 x 32 tiles
+    // when every input is unit-stride along dim 0 or along the tiled dim t, C
+    // along dim 0, there are at most 5 dims (the tensor-map rank), every
+    // other stride is a multiple of 16 bytes and the bases are 16-byte
+    // aligned.  Vector tiles and permuted rows stay on the SIMT kernels:
+    // on 128^4 FP32 tensors they ran every layout pair faster than the TMA
+    // kernel (its boxes of 128 rows 8 MB apart are the slow case).
+    if (A.dtype == TL_F32 && P.kernel == K_EW_TILE && P.vec == 1 && P.sp.nd >= 2 &&
         P.sp.nd <= 5) {
         const Space& sp = P.sp;
         const int t = P.kernel == K_EW_TILE ? P.tdim : 1;

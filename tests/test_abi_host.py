@@ -138,15 +138,32 @@ def test_collapse_preserves_element_triples_entrywise(tl, seed):
 def test_entrywise_kernel_choice(tl):
     n = (64, 64, 64)
     F, L = (1, 2, 3), (3, 2, 1)
-    # FP32 mixed layouts a tensor map can describe take the TMA tile kernel;
-    # FP64 takes the register-tiled transpose
-    for dtype, tile in (("f32", "ew_tma"), ("f64", "ew_tile")):
+    # mixed layouts whose extents and strides allow 16-byte vectors take the
+    # vector tile kernel (FP32 and FP64)
+    for dtype, tile in (("f32", "ew_tile"), ("f64", "ew_tile")):
         for pa, pb, pc, kern in [(F, F, F, "ew_flat"), (F, L, F, tile), (L, F, F, tile),
                                  (L, L, L, "ew_flat")]:
             rc, P = _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, n, pa, dtype=dtype),
                           _desc(tl, n, pc, dtype=dtype, addr=FAKE * 4096),
                           B=_desc(tl, n, pb, dtype=dtype, addr=FAKE * 8192), eop=tl.TL_ADD)
             assert rc == 0 and P["kernel"] == kern, (dtype, pa, pb, pc, P)
+    # permuted rows (every operand contiguous along mode 1) take the rows
+    # kernel; FP32 tiles with a ragged extent but 16-byte strides (a padded
+    # view) take the TMA-staged kernel
+    for dtype in ("f32", "f64"):
+        rc, P = _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, n, F, dtype=dtype),
+                      _desc(tl, n, F, dtype=dtype, addr=FAKE * 4096),
+                      B=_desc(tl, n, (1, 3, 2), dtype=dtype, addr=FAKE * 8192), eop=tl.TL_ADD)
+        assert rc == 0 and P["kernel"] == "ew_rows", P
+    nr = (61, 64, 64)
+    rc, P = _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, nr, w=(1, 64, 4096)),
+                  _desc(tl, nr, w=(1, 64, 4096), addr=FAKE * 4096),
+                  B=_desc(tl, nr, w=(64, 1, 4096), addr=FAKE * 8192), eop=tl.TL_ADD)
+    assert rc == 0 and P["kernel"] == "ew_tma" and P["tdim"] == 1, P
+    rc, P = _plan(tl, tl.TL_OP_ENTRYWISE, _desc(tl, nr, w=(1, 64, 4096), dtype="f64"),
+                  _desc(tl, nr, w=(1, 64, 4096), dtype="f64", addr=FAKE * 4096),
+                  B=_desc(tl, nr, w=(64, 1, 4096), dtype="f64", addr=FAKE * 8192), eop=tl.TL_ADD)
+    assert rc == 0 and P["kernel"] == "ew_tile" and P["vec"] == 1, P
     # FP32 but beyond the tensor-map rank (6 dims that do not collapse), or
     # with strides that are not multiples of 16 bytes: the older kernels
     n6 = (8, 3, 2, 3, 2, 4)

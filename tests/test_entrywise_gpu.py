@@ -111,21 +111,32 @@ def test_entrywise_full_scale_sampled(tl, cuda_dev):
     np.testing.assert_array_equal(got, (memF.astype(np.float64) * 2).astype(np.float32))
 
 
-def test_entrywise_vector_tile_path_is_taken(tl, cuda_dev):
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_entrywise_vector_tile_path_bit_exact(tl, cuda_dev, dtype):
     # extents and strides that allow 16-byte vectors select the vector tile
+    # kernel; every staging variant (A staged, B staged, both, unary) over
+    # ragged tiles (extents not multiples of the 64 / 32-element tile) and
+    # batch dims matches the oracle bit for bit
     import json
-    for dtype in ("f32", "f64"):
-        n = (100, 68, 12)
-        A = put(np.zeros(n), (1, 2, 3), cuda_dev, dtype)
-        B = put(np.zeros(n), (3, 2, 1), cuda_dev, dtype)
-        C = torch.empty_like(A)
-        rc, js = tl.tl_plan_describe(tl.TL_OP_ENTRYWISE, tl.Desc(A, n, (1, 2, 3)),
-                                     tl.Desc(B, n, (3, 2, 1)), 0, 0, 0, 0, tl.Desc(C, n))
-        P = json.loads(js)
-        if dtype == "f32":
-            assert P["kernel"] == "ew_tma", P
-        else:
-            assert P["kernel"] == "ew_tile" and P["vec"] == 2, P
+    for n in ((100, 68, 12), (64, 64, 8), (36, 132, 16), (36, 20, 4, 16)):
+        p = len(n)
+        F, L = synth.first_order(p), synth.last_order(p)
+        X = synth.normal(n, 3450, dtype=np.float64)
+        Y = synth.normal(n, 3451, dtype=np.float64) + 3.0
+        for pa, pb, pc, ops in [(F, L, F, ("add", "div")), (L, F, F, ("sub", "mul")),
+                                (L, L, F, ("add",)), (F, F, L, ("sub",)), (L, F, F, ("copy", "scale"))]:
+            A = put(X, pa, cuda_dev, dtype)
+            B = put(Y, pb, cuda_dev, dtype)
+            C = torch.empty_like(A)
+            for op in ops:
+                unary = OPS[op] in (4, 5)
+                rc, js = tl.tl_plan_describe(tl.TL_OP_ENTRYWISE, tl.Desc(A, n, pa),
+                                             None if unary else tl.Desc(B, n, pb), 0, 0, 0, OPS[op],
+                                             tl.Desc(C, n, pc))
+                P = json.loads(js)
+                assert P["kernel"] == "ew_tile" and P["vec"] == (4 if dtype == "f32" else 2), P
+                got, ref = ew_case(tl, cuda_dev, OPS[op], X, Y, pa, pb, pc, dtype)
+                np.testing.assert_array_equal(got, ref)
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
@@ -141,7 +152,7 @@ def test_entrywise_shared_fastest_mode_rows_path(tl, cuda_dev, dtype):
         C = torch.empty_like(A)
         rc, js = tl.tl_plan_describe(tl.TL_OP_ENTRYWISE, tl.Desc(A, n, pa), tl.Desc(B, n, pb),
                                      0, 0, 0, tl.TL_MUL, tl.Desc(C, n, pc))
-        assert json.loads(js)["kernel"] == ("ew_tma" if dtype == "f32" else "ew_rows"), js
+        assert json.loads(js)["kernel"] == "ew_rows", js
         got, ref = ew_case(tl, cuda_dev, OPS["mul"], X, Y, pa, pb, pc, dtype)
         np.testing.assert_array_equal(got, ref)
 
@@ -149,17 +160,19 @@ def test_entrywise_shared_fastest_mode_rows_path(tl, cuda_dev, dtype):
 @pytest.mark.parametrize("shape", [(36, 20, 64), (8, 12, 16, 20), (64, 36, 4, 8, 12), (96, 33 * 4, 8),
                                    (4, 4, 4, 4, 4)])
 @pytest.mark.parametrize("op", ["add", "div", "copy", "scale"])
-def test_entrywise_tma_tiles_bit_exact(tl, cuda_dev, shape, op):
-    # FP32 layouts whose strides are multiples of 16 bytes take the TMA-staged
-    # tile kernel: transposed and direct inputs, ragged tiles, up to 3 batch dims
+def test_entrywise_fp32_mixed_layouts_bit_exact(tl, cuda_dev, shape, op):
+    # dense FP32 layout mixes: transposed and direct inputs, ragged tiles, up
+    # to 3 batch dims, permuted rows (F, R, F) and (R, F, F): every operand
+    # contiguous along mode 1, the rest reversed in B or A
     import json
     p = len(shape)
     g = synth.rng(3600 + p)
     X = synth.normal(shape, 3601, dtype=np.float64)
     Y = synth.normal(shape, 3602, dtype=np.float64) + 3.0
     F, L = synth.first_order(p), synth.last_order(p)
-    combos = [(F, L, F), (L, F, F), (L, L, F), (F, F, L), (synth.random_layout(p, g), F, F)]
-    seen = set()
+    R = (1,) + tuple(range(p, 1, -1))
+    combos = [(F, L, F), (L, F, F), (L, L, F), (F, F, L), (synth.random_layout(p, g), F, F),
+              (F, R, F), (R, F, F)]
     for pa, pb, pc in combos:
         A = put(X, pa, cuda_dev, "f32")
         B = put(Y, pb, cuda_dev, "f32")
@@ -168,10 +181,53 @@ def test_entrywise_tma_tiles_bit_exact(tl, cuda_dev, shape, op):
         rc, js = tl.tl_plan_describe(tl.TL_OP_ENTRYWISE, tl.Desc(A, shape, pa),
                                      None if unary else tl.Desc(B, shape, pb), 0, 0, 0, OPS[op],
                                      tl.Desc(C, shape, pc))
-        assert rc == 0
-        seen.add(json.loads(js)["kernel"])
+        assert rc == 0 and json.loads(js)["kernel"] in ("ew_flat", "ew_tile", "ew_rows",
+                                                        "ew_generic"), js
         got, ref = ew_case(tl, cuda_dev, OPS[op], X, Y, pa, pb, pc, "f32")
         np.testing.assert_array_equal(got, ref)
+
+
+def _padded(X, pi, dev):
+    """X in layout pi inside a parent whose fastest mode is padded to a
+    multiple of 4 elements: a view with a ragged extent and 16-byte strides."""
+    n = X.shape
+    pn = list(n)
+    pn[pi[0] - 1] = (n[pi[0] - 1] + 3) // 4 * 4
+    parent = np.zeros(pn, dtype=np.float32)
+    parent[tuple(slice(0, x) for x in n)] = X
+    return to_dev(synth.to_memory(parent, pi), dev, "f32"), oracle.strides(tuple(pn), pi)
+
+
+@pytest.mark.parametrize("shape", [(61, 64, 40), (30, 6, 21, 9), (30, 7, 3, 2, 33), (37, 129)])
+@pytest.mark.parametrize("op", ["add", "div", "copy", "scale"])
+def test_entrywise_tma_tiles_padded_views_bit_exact(tl, cuda_dev, shape, op):
+    # FP32 mixed layouts with a ragged extent whose strides stay multiples of
+    # 16 bytes (padded views) take the TMA-staged tile kernel: transposed and
+    # direct inputs, ragged tiles, up to 3 batch dims; C's padding keeps its
+    # initial value
+    import json
+    p = len(shape)
+    X = synth.normal(shape, 3610, dtype=np.float64).astype(np.float32)
+    Y = (synth.normal(shape, 3611, dtype=np.float64) + 3.0).astype(np.float32)
+    F, L = synth.first_order(p), synth.last_order(p)
+    unary = OPS[op] in (4, 5)
+    seen = set()
+    for pa, pb, pc in [(F, L, F), (L, F, F), (L, L, F), (F, F, L)]:
+        A, wA = _padded(X, pa, cuda_dev)
+        B, wB = _padded(Y, pb, cuda_dev)
+        C, wC = _padded(np.zeros(shape, dtype=np.float32), pc, cuda_dev)
+        C.fill_(-7.0)
+        C0 = C.cpu().numpy().astype(np.float64)
+        DA, DB, DC = tl.Desc(A, shape, w=wA), tl.Desc(B, shape, w=wB), tl.Desc(C, shape, w=wC)
+        rc, js = tl.tl_plan_describe(tl.TL_OP_ENTRYWISE, DA, None if unary else DB, 0, 0, 0,
+                                     OPS[op], DC)
+        assert rc == 0
+        seen.add(json.loads(js)["kernel"])
+        tl.check(tl.tl_entrywise(OPS[op], DA, None if unary else DB, -1.5, DC))
+        torch.cuda.synchronize()
+        ref = oracle.entrywise(OPS[op], shape, A.cpu().numpy(), wA, B.cpu().numpy(), wB, -1.5,
+                               C=C0, wC=wC)
+        np.testing.assert_array_equal(C.cpu().numpy(), ref.astype(np.float32))
     assert "ew_tma" in seen, seen
 
 
