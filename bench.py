@@ -61,7 +61,7 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=1 << 18,
                     help="outputs per ttv/ttm op in the CPU-oracle sample")
     ap.add_argument("--profile-case", default=None,
-                    choices=["ttm_tc_x64", "sgemm_384", "batch_512", "ew_tma_96"],
+                    choices=["ttm_tc_x64", "sgemm_384", "batch_512", "ew_add_96"],
                     help="run one small case three times and exit (the workloads the ncu "
                          "captures under profiles/ use; no JSON line)")
     ap.add_argument("--no-batch", action="store_true")
@@ -515,8 +515,8 @@ def profile_case(name):
     it): ttm_tc_x64 = split-BF16x3 ttm of a 512^3 FP32 tensor by a 64 x 512
     matrix along mode 1; sgemm_384 = FP32 ttm of 384^3 by 384 x 384 along mode
     1; batch_512 = 512 operations of the batch recipe in one persistent
-    launch (default unit choices); ew_tma_96 = the first-order + last-order
-    add of two 96^4 FP32 tensors."""
+    launch (default unit choices); ew_add_96 = the first-order + last-order
+    add of two 96^4 FP32 tensors (the vector tile kernel)."""
     import torch
     import synth
     from paper_1711_10912_gb300 import build as tlbuild

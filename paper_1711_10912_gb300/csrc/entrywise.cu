@@ -56,8 +56,9 @@ constexpr int kThreads = 256;
 
 // Decodes tile index blk into its tile coordinates along dim 0 and t and the
 // operands' offsets of its batch index.  NB >= 0 is the number of batch dims
-// known at compile time (unrolled, the division tables read at fixed
-// offsets); NB < 0 reads it from the arguments.
+// known at compile time (the loop unrolls and reads its tables at fixed
+// offsets; a bound with a run-time count instead measured 15 % slower on the
+// 128^4 adds); NB < 0 takes any number.
 template <int NB>
 __device__ __forceinline__ void tile_decode(const EwArgs& a, int64_t blk, int64_t& bt0,
                                             int64_t& bt1, int64_t* base)
@@ -297,6 +298,14 @@ __global__ void __launch_bounds__(kThreads) ew_tile_kernel(const EwArgs a, int64
     }
 }
 
+// Threads of a vector-tile CTA for a T0 x TT tile: four 16-byte vectors per
+// thread and operand for FP32, two for FP64.
+template <typename T>
+__host__ __device__ constexpr int tile_threads(int t0, int tt)
+{
+    return t0 * tt / (16 / (int)sizeof(T)) / (sizeof(T) == 4 ? 4 : 2);
+}
+
 // Vectorised tile kernel: TILE x TILE elements over dims (0, t), TILE = 64
 // for FP32 and 32 for FP64 (256-byte rows either way), one tile per CTA
 // (a grid-stride loop only when the tiles outnumber the largest grid).
@@ -317,17 +326,19 @@ __global__ void __launch_bounds__(kThreads) ew_tile_kernel(const EwArgs a, int64
 // kernel ran them at 5.0-6.8 (its boxes of 128 rows 8 MB apart are the slow
 // case), and storing each load at once, or capping binary operations at 6
 // CTAs per SM, left the add of the reversed layouts at 5.3-6.0.
-template <typename T, bool SA, bool SB, bool UN, int NB>
-__global__ void __launch_bounds__(kThreads, UN ? 6 : 4) ew_tile_vec_kernel(const EwArgs a, int64_t total)
+template <typename T, int T0, int TT, bool SA, bool SB, bool UN, int NB>
+__global__ void __launch_bounds__(tile_threads<T>(T0, TT), (UN ? 1536 : 1024) / tile_threads<T>(T0, TT))
+ew_tile_vec_kernel(const EwArgs a, int64_t total)
 {
     constexpr int VEC = 16 / sizeof(T);
-    constexpr int TILE = 16 * VEC;
-    constexpr int LD = TILE + 1;                       // padded shared row
-    constexpr int NV = TILE * TILE / VEC / kThreads;   // vectors per thread and operand
-    static_assert(NV * VEC * kThreads == TILE * TILE, "tile / block mismatch");
+    constexpr int NT = tile_threads<T>(T0, TT);          // threads of the CTA
+    constexpr int LD = TT + 1;                            // padded shared row
+    constexpr int NV = T0 * TT / VEC / NT;                // vectors per thread and operand
+    constexpr int HALVES = T0 / (8 * VEC);                // 128-byte pieces of a dim-0 row
+    static_assert(NV * VEC * NT == T0 * TT && (HALVES == 1 || HALVES == 2), "tile shape");
     extern __shared__ __align__(16) unsigned char ew_smem[];
     T* const tA = reinterpret_cast<T*>(ew_smem);
-    T* const tB = tA + (SA ? TILE * LD : 0);
+    T* const tB = tA + (SA ? T0 * LD : 0);
     const T* __restrict__ A = static_cast<const T*>(a.A);
     const T* __restrict__ B = static_cast<const T*>(a.B);
     T* __restrict__ C = static_cast<T*>(a.C);
@@ -339,15 +350,15 @@ __global__ void __launch_bounds__(kThreads, UN ? 6 : 4) ew_tile_vec_kernel(const
     for (int64_t blk = blockIdx.x; blk < total; blk += gridDim.x) {
         int64_t bt0, bt1, base[3];
         tile_decode<NB>(a, blk, bt0, bt1, base);
-        const int64_t i0b = bt0 * TILE, itb = bt1 * TILE;
+        const int64_t i0b = bt0 * T0, itb = bt1 * TT;
         T xa[SA ? 1 : NV][VEC], xb[(SB || UN) ? 1 : NV][VEC];
         if constexpr (UN) {
             // unary (one staged input): each load is followed by its
             // shared-memory store
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                const int v = threadIdx.x + kThreads * k;
-                const int ts = (v % (TILE / VEC)) * VEC, xs = v / (TILE / VEC);
+                const int v = threadIdx.x + NT * k;
+                const int ts = (v % (TT / VEC)) * VEC, xs = v / (TT / VEC);
                 const int64_t i0s = i0b + xs, its = itb + ts;
                 if (i0s < n0 && its < nt) {
                     T x[VEC];
@@ -363,12 +374,13 @@ __global__ void __launch_bounds__(kThreads, UN ? 6 : 4) ew_tile_vec_kernel(const
             // every global load of the tile first, then the shared-memory stores
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                const int v = threadIdx.x + kThreads * k;
-                // staged order: TILE / VEC vectors along t per dim-0 row
-                const int ts = (v % (TILE / VEC)) * VEC, xs = v / (TILE / VEC);
-                // write order: 8 vectors along dim 0, 4 t-rows, 2 halves of dim 0
-                const int xd = ((v >> 5) & 1) * 8 * VEC + (v & 7) * VEC;
-                const int td = (v >> 6) * 4 + ((v >> 3) & 3);
+                const int v = threadIdx.x + NT * k;
+                // staged order: TT / VEC vectors along t per dim-0 row
+                const int ts = (v % (TT / VEC)) * VEC, xs = v / (TT / VEC);
+                // write order: 8 vectors along dim 0, 4 t-rows, the 128-byte
+                // pieces of dim 0
+                const int xd = ((v >> 5) % HALVES) * 8 * VEC + (v & 7) * VEC;
+                const int td = (v >> 5) / HALVES * 4 + ((v >> 3) & 3);
                 const int64_t i0s = i0b + xs, its = itb + ts, i0d = i0b + xd, itd = itb + td;
                 oks[k] = i0s < n0 && its < nt;
                 const bool okd = i0d < n0 && itd < nt;
@@ -392,8 +404,8 @@ __global__ void __launch_bounds__(kThreads, UN ? 6 : 4) ew_tile_vec_kernel(const
             }
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                const int v = threadIdx.x + kThreads * k;
-                const int ts = (v % (TILE / VEC)) * VEC, xs = v / (TILE / VEC);
+                const int v = threadIdx.x + NT * k;
+                const int ts = (v % (TT / VEC)) * VEC, xs = v / (TT / VEC);
                 if (oks[k]) {
 #pragma unroll
                     for (int e = 0; e < VEC; ++e) {
@@ -406,9 +418,9 @@ __global__ void __launch_bounds__(kThreads, UN ? 6 : 4) ew_tile_vec_kernel(const
         }
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            const int v = threadIdx.x + kThreads * k;
-            const int xd = ((v >> 5) & 1) * 8 * VEC + (v & 7) * VEC;
-            const int td = (v >> 6) * 4 + ((v >> 3) & 3);
+            const int v = threadIdx.x + NT * k;
+            const int xd = ((v >> 5) % HALVES) * 8 * VEC + (v & 7) * VEC;
+            const int td = (v >> 5) / HALVES * 4 + ((v >> 3) & 3);
             const int64_t i0 = i0b + xd, it = itb + td;
             if (i0 < n0 && it < nt) {
                 T r[VEC];
@@ -428,17 +440,43 @@ __global__ void __launch_bounds__(kThreads, UN ? 6 : 4) ew_tile_vec_kernel(const
 }
 
 // Launches the vector tile kernel for staging kind vkind (0 unary, 1 both
-// inputs staged, 2 A staged, 3 B staged) and NB batch dims.
-template <typename T, int NB>
+// inputs staged, 2 A staged, 3 B staged), a T0 x TT tile and NB batch dims
+// (-1: any number).
+template <typename T, int T0, int TT, int NB>
 void launch_tile_vec(int vkind, int grid, size_t smem, cudaStream_t st, const EwArgs& a,
                      int64_t total)
 {
+    constexpr int NT = tile_threads<T>(T0, TT);
     switch (vkind) {
-    case 0: ew_tile_vec_kernel<T, true, false, true, NB><<<grid, kThreads, smem, st>>>(a, total); break;
-    case 1: ew_tile_vec_kernel<T, true, true, false, NB><<<grid, kThreads, smem, st>>>(a, total); break;
-    case 2: ew_tile_vec_kernel<T, true, false, false, NB><<<grid, kThreads, smem, st>>>(a, total); break;
-    default: ew_tile_vec_kernel<T, false, true, false, NB><<<grid, kThreads, smem, st>>>(a, total); break;
+    case 0: ew_tile_vec_kernel<T, T0, TT, true, false, true, NB><<<grid, NT, smem, st>>>(a, total); break;
+    case 1: ew_tile_vec_kernel<T, T0, TT, true, true, false, NB><<<grid, NT, smem, st>>>(a, total); break;
+    case 2: ew_tile_vec_kernel<T, T0, TT, true, false, false, NB><<<grid, NT, smem, st>>>(a, total); break;
+    default: ew_tile_vec_kernel<T, T0, TT, false, true, false, NB><<<grid, NT, smem, st>>>(a, total); break;
     }
+}
+
+template <typename T, int T0, int TT>
+void launch_tile_vec_nb(int nb, int vkind, int grid, size_t smem, cudaStream_t st,
+                        const EwArgs& a, int64_t total)
+{
+    switch (nb) {
+    case 0: launch_tile_vec<T, T0, TT, 0>(vkind, grid, smem, st, a, total); break;
+    case 1: launch_tile_vec<T, T0, TT, 1>(vkind, grid, smem, st, a, total); break;
+    case 2: launch_tile_vec<T, T0, TT, 2>(vkind, grid, smem, st, a, total); break;
+    case 3: launch_tile_vec<T, T0, TT, 3>(vkind, grid, smem, st, a, total); break;
+    default: launch_tile_vec<T, T0, TT, -1>(vkind, grid, smem, st, a, total); break;
+    }
+}
+
+// Tile edge (elements) along one dim: 256 bytes, or 128 when that fills the
+// ragged last tile better (an extent of 96 FP32 elements: three 32-element
+// tiles instead of two of 64, the second half empty).
+template <typename T>
+int tile_edge(int64_t n)
+{
+    const int64_t big = 256 / sizeof(T), small = 128 / sizeof(T);
+    const int64_t tb = (n + big - 1) / big * big, ts = (n + small - 1) / small * small;
+    return (int)(ts < tb ? small : big);
 }
 
 int grid_for(int64_t threads, int num_sms)
@@ -472,15 +510,17 @@ int launch_typed(const EwPlan& P, const void* A, const void* B, double alpha, vo
         if (P.vec == V) ew_flat_kernel<T, V, U><<<chunk_grid(P.N / V), kThreads, 0, st>>>(a);
         else ew_flat_kernel<T, 1, U><<<chunk_grid(P.N), kThreads, 0, st>>>(a);
     } else if (P.kernel == K_EW_TILE) {
-        const int tile = P.vec > 1 ? 16 * V : kTile;
-        int64_t tiles0 = (P.sp.d[0].n + tile - 1) / tile;
-        int64_t tiles1 = (P.sp.d[P.tdim].n + tile - 1) / tile;
-        int64_t batch = P.N / (P.sp.d[0].n * P.sp.d[P.tdim].n);
-        int64_t total = tiles0 * tiles1 * batch;
         const bool unary = P.op == TL_COPY || P.op == TL_SCALE;
         const bool sa = P.sp.d[P.tdim].s[0] < P.sp.d[0].s[0];
         const bool sb = !unary && P.sp.d[P.tdim].s[1] < P.sp.d[0].s[1];
-        if (P.vec > 1 && (sa || sb)) {
+        const bool vec = P.vec > 1 && (sa || sb);
+        const int t0 = vec ? tile_edge<T>(P.sp.d[0].n) : kTile;
+        const int tt = vec ? tile_edge<T>(P.sp.d[P.tdim].n) : kTile;
+        int64_t tiles0 = (P.sp.d[0].n + t0 - 1) / t0;
+        int64_t tiles1 = (P.sp.d[P.tdim].n + tt - 1) / tt;
+        int64_t batch = P.N / (P.sp.d[0].n * P.sp.d[P.tdim].n);
+        int64_t total = tiles0 * tiles1 * batch;
+        if (vec) {
             // tile decode tables: tiles along dim 0 and t, then the batch dims
             a.ntile0 = (uint32_t)tiles0;
             a.ntile1 = (uint32_t)tiles1;
@@ -501,15 +541,14 @@ int launch_typed(const EwPlan& P, const void* A, const void* B, double alpha, vo
             // dim of the two (the planner's vector conditions make it unit
             // stride there)
             const int grid = (int)(total < INT32_MAX ? total : INT32_MAX);
-            const size_t smem = (size_t)((sa ? 1 : 0) + (sb ? 1 : 0)) * tile * (tile + 1) * sizeof(T);
+            const size_t smem = (size_t)((sa ? 1 : 0) + (sb ? 1 : 0)) * t0 * (tt + 1) * sizeof(T);
             const int vkind = unary ? 0 : (sa && sb) ? 1 : sa ? 2 : 3;
-            switch (a.idx32 ? a.nb : -1) {
-            case 0: launch_tile_vec<T, 0>(vkind, grid, smem, st, a, total); break;
-            case 1: launch_tile_vec<T, 1>(vkind, grid, smem, st, a, total); break;
-            case 2: launch_tile_vec<T, 2>(vkind, grid, smem, st, a, total); break;
-            case 3: launch_tile_vec<T, 3>(vkind, grid, smem, st, a, total); break;
-            default: launch_tile_vec<T, -1>(vkind, grid, smem, st, a, total); break;
-            }
+            const int nb = a.idx32 ? a.nb : -1;
+            constexpr int B = 256 / sizeof(T), S = 128 / sizeof(T);
+            if (t0 == B && tt == B) launch_tile_vec_nb<T, B, B>(nb, vkind, grid, smem, st, a, total);
+            else if (t0 == B) launch_tile_vec_nb<T, B, S>(nb, vkind, grid, smem, st, a, total);
+            else if (tt == B) launch_tile_vec_nb<T, S, B>(nb, vkind, grid, smem, st, a, total);
+            else launch_tile_vec_nb<T, S, S>(nb, vkind, grid, smem, st, a, total);
         } else {
             const int64_t cap = (int64_t)num_sms * 8;
             const int grid = (int)(total < cap ? total : cap);
