@@ -61,7 +61,7 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=1 << 18,
                     help="outputs per ttv/ttm op in the CPU-oracle sample")
     ap.add_argument("--profile-case", default=None,
-                    choices=["ttm_tc_x64", "sgemm_384", "batch_512", "ew_add_96"],
+                    choices=["ttm_tc_x64", "sgemm_384", "batch_512", "ew_add_128x48"],
                     help="run one small case three times and exit (the workloads the ncu "
                          "captures under profiles/ use; no JSON line)")
     ap.add_argument("--no-batch", action="store_true")
@@ -515,8 +515,10 @@ def profile_case(name):
     it): ttm_tc_x64 = split-BF16x3 ttm of a 512^3 FP32 tensor by a 64 x 512
     matrix along mode 1; sgemm_384 = FP32 ttm of 384^3 by 384 x 384 along mode
     1; batch_512 = 512 operations of the batch recipe in one persistent
-    launch (default unit choices); ew_add_96 = the first-order + last-order
-    add of two 96^4 FP32 tensors (the vector tile kernel)."""
+    launch (default unit choices); ew_add_128x48 = the first-order +
+    last-order add of two 128 x 48 x 128 x 128 FP32 tensors (0.4 GB each: the
+    vector tile kernel with the 64 x 64 tiles and two batch dims of the
+    128^4 add)."""
     import torch
     import synth
     from paper_1711_10912_gb300 import build as tlbuild
@@ -544,8 +546,8 @@ def profile_case(name):
         keep.append(batch)
         fn = lambda: tl.check(tl.tl_batch_run(batch, sh))
     else:
-        n = (96,) * 4
-        N = 96 ** 4
+        n = (128, 48, 128, 128)
+        N = 128 ** 3 * 48
         A = synth.device_normal(torch, N, 71_002, torch.float32, dev)
         B = synth.device_normal(torch, N, 71_003, torch.float32, dev)
         C = torch.empty(N, dtype=torch.float32, device=dev)
