@@ -307,10 +307,12 @@ __device__ void unit_ttm(const BOp& op, int64_t m0, uint8_t* smem)
 }
 
 // ttm with the whole J x n_q matrix in shared memory (n_q <= 64, J <= 64 for
-// FP32, J <= 32 for FP64): one row of A per thread, JB <= 32 of its outputs
-// kept in registers per pass (a second pass re-reads the row, from L1/L2, when
-// J > 32), k unrolled 8 deep so eight loads of A are in flight per thread, B
-// read as 16-byte broadcasts.
+// FP32, J <= 32 for FP64): one row of A per thread, JB <= 16 of its outputs
+// kept in registers per pass (further passes re-read the row, from L1/L2,
+// when J > 16: on the 4096-operation batch recipe that ran the small ttm
+// operations in 1.69 ms against 1.84 with 32 columns per pass), k unrolled 8
+// deep so eight loads of A are in flight per thread, B read as 16-byte
+// broadcasts.
 template <typename T, int JB>
 __device__ void unit_ttm_small(const BOp& op, int64_t e0, int64_t e1, uint8_t* smem)
 {
@@ -433,7 +435,7 @@ __device__ void run_unit(const BOp& op, int64_t u, uint8_t* smem)
         } else if (op.J <= 4) unit_ttm_small<T, 4>(op, e0, e1, smem);
         else if (op.J <= 8) unit_ttm_small<T, 8>(op, e0, e1, smem);
         else if (op.J <= 16) unit_ttm_small<T, 16>(op, e0, e1, smem);
-        else unit_ttm_small<T, (sizeof(T) == 8 ? 16 : 32)>(op, e0, e1, smem);
+        else unit_ttm_small<T, 16>(op, e0, e1, smem);
         break;
     default: unit_ew<T>(op, e0, e1); break;
     }
