@@ -6,13 +6,14 @@
 // is one M x J x n_q matrix product.  This kernel is the FP32 one, built for
 // the FMA issue rate:
 //  - one CTA of 256 threads per SM computes a 128 x 256 (rows x j) tile when
-//    J > 128, else a 256 x 128 tile; each thread holds an 8 x 16 (or 16 x 8)
-//    block of outputs in registers, built from 4 x 4 sub-blocks 64 apart so
-//    that its operands are 16-byte shared-memory reads.  Each k step then
-//    reads 24 floats per thread for 128 FMAs: the SM's shared-memory port
-//    (32 lanes x 4 bytes per cycle) delivers them in 3/4 of the time the FMA
-//    pipes (128 lanes per cycle) take, where an 8 x 8 block would need all
-//    of it;
+//    J > 128, a 256 x 128 tile when 64 < J <= 128, and a 512 x 64 tile when
+//    J <= 64 (no idle columns for small J); each thread holds an 8 x 16,
+//    16 x 8 or 32 x 4 block of outputs in registers, built from 4 x 4
+//    sub-blocks 64 apart so that its operands are 16-byte shared-memory
+//    reads.  Each k step then reads 24 floats per thread for 128 FMAs (36
+//    for the 512 x 64 tile): the SM's shared-memory port (32 lanes x 4 bytes
+//    per cycle) delivers them in 3/4 of the time the FMA pipes (128 lanes per
+//    cycle) take, where an 8 x 8 block would need all of it;
 //  - k advances in slabs of 16: the next slab's A and B tiles are loaded from
 //    global memory into registers while the current slab is multiplied out
 //    of shared memory, then stored into the second of two shared-memory
@@ -78,14 +79,17 @@ struct Slab {
     // LD_K4: vector v of this thread holds row k4_row(v), k = k4_k(v)..+3.
     // Each pass covers 128 rows (two threads per row, 8 k values apart from
     // the next pass's pair), so a warp's transposing stores touch rows 4
-    // banks apart at two k values 4 apart: 32 distinct banks.
+    // banks apart at two k values 4 apart: 32 distinct banks.  A 64-row slab
+    // takes four threads per row instead (one pass covers its 64 rows x 16 k).
+    static constexpr int kTpr = NR >= 128 ? 2 : 4;       // threads per row in a pass
+    static_assert(NR >= 64 && NR % (kThreads / kTpr) == 0, "LD_K4 slab rows");
     __device__ __forceinline__ static int k4_row(int v)
     {
-        return (v / (BK / 8)) * 128 + (threadIdx.x >> 1);
+        return (v / (BK / (4 * kTpr))) * (kThreads / kTpr) + (int)threadIdx.x / kTpr;
     }
     __device__ __forceinline__ static int k4_k(int v)
     {
-        return (v % (BK / 8)) * 8 + (threadIdx.x & 1) * 4;
+        return (v % (BK / (4 * kTpr))) * (4 * kTpr) + ((int)threadIdx.x % kTpr) * 4;
     }
 
     template <typename RowOff>
@@ -329,8 +333,16 @@ int sgemm_bmode(const TtmPlan& P, const void* B)
     return LD_SCALAR;
 }
 
-// 128 x 256 tiles when J spans more than 128 columns, else 256 x 128
+// 128 x 256 tiles when J spans more than 128 columns, 512 x 64 when it spans
+// at most 64, else 256 x 128
 bool sgemm_wide(const TtmPlan& P) { return P.J > 128; }
+bool sgemm_thin(const TtmPlan& P) { return P.J <= 64; }
+
+void sgemm_tile(const TtmPlan& P, int64_t& tm, int64_t& tn)
+{
+    tm = sgemm_wide(P) ? 128 : sgemm_thin(P) ? 512 : 256;
+    tn = sgemm_wide(P) ? 256 : sgemm_thin(P) ? 64 : 128;
+}
 
 int sgemm_cmode(const TtmPlan& P, const void* C, bool split)
 {
@@ -357,20 +369,22 @@ std::string ttm_sgemm_describe(const TtmPlan& P, const void* A, const void* C, b
     }
     return std::string("{\"a\":\"") + ld[sgemm_amode(P, A)] + "\",\"b\":\"" +
            ld[sgemm_bmode(Q, aligned_b)] + "\",\"c\":\"" + stn[sgemm_cmode(P, C, split)] +
-           "\",\"tile\":[" + (sgemm_wide(P) ? "128,256" : "256,128") + "]}";
+           "\",\"tile\":[" + (sgemm_wide(P) ? "128,256" : sgemm_thin(P) ? "512,64" : "256,128") + "]}";
 }
 
 int64_t sgemm_tiles(const TtmPlan& P)
 {
-    const int64_t tm = sgemm_wide(P) ? 128 : 256, tn = sgemm_wide(P) ? 256 : 128;
+    int64_t tm, tn;
+    sgemm_tile(P, tm, tn);
     return ((P.M + tm - 1) / tm) * ((P.J + tn - 1) / tn);
 }
 
 int launch_ttm_sgemm(const TtmPlan& P, const void* A, const void* B, void* C, int accumulate,
                      void* ws, int64_t splits, int64_t kchunk, int num_sms, cudaStream_t st)
 {
-    const bool wide = sgemm_wide(P);
-    const int64_t tm = wide ? 128 : 256, tn = wide ? 256 : 128;
+    const bool wide = sgemm_wide(P), thin = sgemm_thin(P);
+    int64_t tm, tn;
+    sgemm_tile(P, tm, tn);
     SgArgs a{};
     a.A = static_cast<const float*>(A);
     a.B = static_cast<const float*>(B);
@@ -408,8 +422,13 @@ int launch_ttm_sgemm(const TtmPlan& P, const void* A, const void* B, void* C, in
         {ttm_sgemm_kernel<LD_R4, LD_K4, 4, 2>, ttm_sgemm_kernel<LD_R4, LD_SCALAR, 4, 2>},
         {ttm_sgemm_kernel<LD_SCALAR, LD_K4, 4, 2>, ttm_sgemm_kernel<LD_SCALAR, LD_SCALAR, 4, 2>},
     };
+    static const KernelFn thin_k[3][2] = {
+        {ttm_sgemm_kernel<LD_K4, LD_K4, 8, 1>, ttm_sgemm_kernel<LD_K4, LD_SCALAR, 8, 1>},
+        {ttm_sgemm_kernel<LD_R4, LD_K4, 8, 1>, ttm_sgemm_kernel<LD_R4, LD_SCALAR, 8, 1>},
+        {ttm_sgemm_kernel<LD_SCALAR, LD_K4, 8, 1>, ttm_sgemm_kernel<LD_SCALAR, LD_SCALAR, 8, 1>},
+    };
     const int bi = a.bmode == LD_K4 ? 0 : 1;
-    const KernelFn fn = wide ? wide_k[amode][bi] : tall_k[amode][bi];
+    const KernelFn fn = wide ? wide_k[amode][bi] : thin ? thin_k[amode][bi] : tall_k[amode][bi];
     // double-buffered A and B slabs, rows padded by 4 floats
     const size_t smem = (size_t)2 * BK * ((tm + 4) + (tn + 4)) * sizeof(float);
     if (smem_optin(reinterpret_cast<const void*>(fn), (int)smem) != TL_OK) return TL_ECUDA;

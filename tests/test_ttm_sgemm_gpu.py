@@ -3,8 +3,8 @@ FP64 oracle, in every way the kernel reads its operands (16-byte vectors
 along k or along contiguous rows, element loads) and writes its output
 (vectors along j or along rows, element stores, split-K partials).
 
-Shapes span several 128 x 256 tiles (J > 128) or 256 x 128 tiles (J <= 128)
-with ragged edges in rows, columns and the contraction (not a multiple of
+Shapes span several 128 x 256 tiles (J > 128), 256 x 128 tiles (64 < J <=
+128) or 512 x 64 tiles (J <= 64) with ragged edges in rows, columns and the contraction (not a multiple of
 the 8-deep k slab).  Bars: integer-valued
 inputs are bit-exact (every partial sum is an integer below 2^24); real
 inputs stay within each element's rounding bound of a length-n_q FP32 dot
@@ -39,6 +39,9 @@ MODES = [
     ((300, 520), 1, 300, (1, 2), (1, 2), False, "k4", "j4"),
     ((300, 260), 1, 100, (1, 2), (1, 2), False, "k4", "j4"),
     ((260, 300), 2, 64, (1, 2), (1, 2), False, "r4", "m4"),
+    ((500, 1100), 1, 60, (1, 2), (1, 2), False, "k4", "j4"),
+    ((1100, 500), 2, 64, (1, 2), (1, 2), False, "r4", "m4"),
+    ((36, 500, 30), 2, 36, (1, 2, 3), (2, 3, 1), True, "r4", "j4"),
 ]
 
 
@@ -58,6 +61,7 @@ def test_sgemm_modes_integer_exact_and_real_bounded(tl, cuda_dev, case):
     d = _plan(tl, cuda_dev, n, q, J, pi_a, pi_c)
     assert d["kernel"] == "ttm_simt" and d["splits"] == 1, d
     assert d["sgemm"]["a"] == amode and d["sgemm"]["c"] == cmode, d
+    assert d["sgemm"]["tile"] == ([128, 256] if J > 128 else [256, 128] if J > 64 else [512, 64]), d
     nq = n[q - 1]
     # integers in [-4, 4]: sums stay below 2^24, so every order of summation is exact
     X = synth.integers(n, 7100 + J, lo=-4, hi=4)
