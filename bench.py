@@ -881,20 +881,34 @@ def measure_serve(tl, torch, dev, sh, nreq, rates, pool=1024, budget=40_000_000_
             sizes.append(3 * N * es)
             keep += [A, Bt, C, DA, DB, DC]
     torch.cuda.synchronize()
-    # warm every call once (plans, workspaces)
+    # warm every call once (plans, workspaces), then time each request alone
+    # on the device: the sum over a trace is the device time the trace needs
+    # when requests run back to back, one at a time
     for fn, args in calls:
         tl.check(fn(*args, sh))
     torch.cuda.synchronize()
+    dev_ms = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for fn, args in calls:
+        e0.record()
+        tl.check(fn(*args, sh))
+        e1.record()
+        e1.synchronize()
+        dev_ms.append(e0.elapsed_time(e1))
+    hbm = load_peaks()[0]["hbm_gbs"]
 
     def pct(x, p):
         return float(np.percentile(np.asarray(x), p)) if x else None
 
     out = {"pool_requests": pool, "requests_per_rate": nreq, "budget_bytes": budget,
-           "streams": streams, "rates": []}
+           "streams": streams, "pool_GB": round(sum(sizes) / 1e9, 2),
+           "pool_device_ms": round(sum(dev_ms), 2), "rates": []}
     for rate in rates:
         g = synth.rng(int(rate))
         pick = g.integers(0, pool, size=nreq)
         arr = np.cumsum(g.exponential(1.0 / rate, size=nreq))
+        trace_bytes = float(sum(sizes[i] for i in pick))
+        trace_dev_s = float(sum(dev_ms[i] for i in pick)) / 1e3
         # ---- continuous batching server
         rc, ctx = tl.tl_ctx_create(budget, streams, tl.TL_CTX_PERSISTENT)
         tl.check(rc, "tl_ctx_create")
@@ -919,7 +933,9 @@ def measure_serve(tl, torch, dev, sh, nreq, rates, pool=1024, budget=40_000_000_
         tl.tl_ctx_destroy(ctx)
         served = {"ops/s": round(nreq / t_end, 1), "p50_ms": round(pct(lat, 50), 3),
                   "p99_ms": round(pct(lat, 99), 3), "batches": batches, "requests": nreq,
-                  "seconds": round(t_end, 2), "max_inflight_GB": round(maxin / 1e9, 3)}
+                  "seconds": round(t_end, 2), "max_inflight_GB": round(maxin / 1e9, 3),
+                  "GB/s": round(trace_bytes / t_end / 1e9, 1),
+                  "frac_hbm": round(trace_bytes / t_end / 1e9 / hbm, 3)}
         # ---- plain: one request at a time, synchronously, on one stream
         lat_p = []
         t0 = time.perf_counter()
@@ -934,8 +950,16 @@ def measure_serve(tl, torch, dev, sh, nreq, rates, pool=1024, budget=40_000_000_
         t_end_p = time.perf_counter() - t0
         plain = {"ops/s": round(nreq / t_end_p, 1), "p50_ms": round(pct(lat_p, 50), 3),
                  "p99_ms": round(pct(lat_p, 99), 3), "requests": nreq,
-                 "seconds": round(t_end_p, 2)}
-        out["rates"].append({"offered_ops/s": rate, "served": served, "plain": plain})
+                 "seconds": round(t_end_p, 2),
+                 "GB/s": round(trace_bytes / t_end_p / 1e9, 1)}
+        # the trace's device time with requests back to back on one stream
+        # (each request's single-call time): the rate one-at-a-time serving
+        # cannot exceed however fast the host is
+        bound = {"device_seconds": round(trace_dev_s, 2),
+                 "ops/s": round(nreq / trace_dev_s, 1),
+                 "GB/s": round(trace_bytes / trace_dev_s / 1e9, 1)}
+        out["rates"].append({"offered_ops/s": rate, "served": served, "plain": plain,
+                             "one_at_a_time_device_bound": bound})
     return out
 
 
