@@ -1498,7 +1498,10 @@ def measure_e2e(tl, torch, wl, args, sh, world, barrier):
                 e.record(s_out)
                 out_free[i] = e
 
-    steps = max(2, min(args.steps, 5))
+    # 20 steps (about a second): the first step's input copy starts on an idle
+    # pipeline and took 28 ms where later ones take 12 while output copies
+    # run; over 5 steps that fill cost 6 ms per step, over 20 it costs 1.5
+    steps = max(2, min(args.steps, 20))
     link_samples = {"d2h_GB/s": link_rates(torch, oM, outs[-1], compute),
                     "h2d_GB/s": link_rates(torch, sets[0]["AF"], hF, compute)}
     step(0)
