@@ -474,7 +474,8 @@ int tl_plan_describe(int32_t op, const tl_tensor* A_, const tl_tensor* B_, uint3
                       (long long)P.J, (long long)P.scq, (long long)P.M, P.tc_variant, splits);
         s = b;
         if (P.kernel == K_TTM_TC) s += "\"tc\":" + ttm_tc_describe(P, C.data) + ",";
-        if (P.kernel == K_TTM_SIMT && P.dtype == TL_F32)
+        if (ttm_skinny(P)) s += "\"skinny\":1,";
+        else if (P.kernel == K_TTM_SIMT && P.dtype == TL_F32)
             s += "\"sgemm\":" + ttm_sgemm_describe(P, A.data, C.data, splits > 1) + ",";
         s += "\"dims\":";
         append_space(s, P.rows);

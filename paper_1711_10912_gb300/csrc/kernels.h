@@ -25,6 +25,8 @@ int ew_status(bool clear);
 // k splits of the SIMT ttm (1 = none) and the k values per split; the
 // workspace of the partial sums; kernels one call launches.
 int64_t ttm_simt_splits(const TtmPlan& P, int num_sms, int64_t* kchunk);
+// a few rows over a long contraction: the split-K skinny kernel takes the call
+bool ttm_skinny(const TtmPlan& P);
 size_t ttm_simt_workspace_bytes(const TtmPlan& P, int num_sms);
 int ttm_simt_launches(const TtmPlan& P, int num_sms);
 // FP32 register-tiled ttm (ttm_sgemm.cu): output tiles of the plan, and the

@@ -240,11 +240,16 @@ int plan_ttm(const Tensor& A, int64_t J, int64_t ldb_row, int64_t ldb_col, uint3
     P.M = P.rows.count();
     P.kernel = K_TTM_SIMT;
     P.tc_variant = 0;
-    // short contractions: a row per thread with the matrix in shared memory
-    // (at most 32 KB of it), unless the tensor-core path takes the call below
+    // short contractions, and narrow outputs (J <= 16) over enough rows to
+    // fill the GPU: a row per thread with the matrix in shared memory (at
+    // most 32 KB of it), unless the tensor-core path takes the call below.
+    // The 64 x 64 tiles of the FP64 kernel would leave 48 of their 64 columns
+    // idle at J <= 16 (an FP64 ttm of 438600 rows, n_q = 232, J = 6 took
+    // 5.6 ms against a 0.49 ms DFMA bound).
     {
         const int64_t Jp = (J + 15) / 16 * 16;
-        if (P.nq <= 64 && P.nq * Jp * (int64_t)A.elem() <= 32 * 1024) P.kernel = K_TTM_ROWS;
+        const bool fits = P.nq * Jp * (int64_t)A.elem() <= 32 * 1024;
+        if (fits && (P.nq <= 64 || (J <= 16 && P.M >= 65536))) P.kernel = K_TTM_ROWS;
     }
     // Tensor-core path: FP32 data in a tensor-core precision, a contraction
     // and output width worth an MMA, and an A that a TMA box can describe

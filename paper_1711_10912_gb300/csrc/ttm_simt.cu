@@ -184,6 +184,78 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmArgs a)
 }
 
 // C(m, j) (+)= sum over splits s = 0, 1, ... of ws[s][m][j].
+// Skinny ttm: a few rows (M <= 16) contracted over a long mode (n_q >= 2048)
+// into at most 64 columns (M x J <= 512 outputs), where any GEMM tile would be
+// almost all idle.  The k range is split across the CTAs; per 64-deep k tile
+// a CTA stages the M rows of A and the J rows of B in shared memory (every
+// load of the tile issued before the stores) and each thread accumulates one
+// or two (m, j) dot products over ascending k; the partial M x J blocks go
+// to ws[s][m][j] and ttm_splitk_reduce adds them in split order.
+constexpr int kSkinnyKT = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) ttm_skinny_kernel(const TtmArgs a)
+{
+    constexpr int KT = kSkinnyKT;
+    constexpr int kLoadsA = 16 * KT / kThreads, kLoadsB = 64 * KT / kThreads;
+    __shared__ T As[16][KT + 1];
+    __shared__ T Bs[64][KT + 1];
+    __shared__ int64_t offA[16];
+    const T* __restrict__ A = static_cast<const T*>(a.A);
+    const T* __restrict__ B = static_cast<const T*>(a.B);
+    T* __restrict__ ws = static_cast<T*>(a.ws);
+    const int tid = threadIdx.x;
+    const int M = (int)a.M, J = (int)a.J, pairs = M * J;
+    if (tid < M) {
+        int64_t off[2];
+        map_offsets<2>(a.rows, tid, 1, off);
+        offA[tid] = off[0];
+    }
+    const int p0 = tid, p1 = tid + kThreads;
+    const int m0 = p0 / J, j0 = p0 - m0 * J, m1 = p1 / J, j1 = p1 - m1 * J;
+    __syncthreads();
+    for (int64_t s = blockIdx.x; s < a.splits; s += gridDim.x) {
+        const int64_t kb = s * a.kchunk, ke = min(a.nq, kb + a.kchunk);
+        T acc0 = T(0), acc1 = T(0);
+        for (int64_t k0 = kb; k0 < ke; k0 += KT) {
+            const int kn = (int)min((int64_t)KT, ke - k0);
+            T va[kLoadsA], vb[kLoadsB];
+#pragma unroll
+            for (int it = 0; it < kLoadsA; ++it) {
+                const int e = tid + kThreads * it, m = e / KT, kk = e % KT;
+                va[it] = (m < M && kk < kn) ? __ldg(A + offA[m] + (k0 + kk) * a.saq) : T(0);
+            }
+#pragma unroll
+            for (int it = 0; it < kLoadsB; ++it) {
+                const int e = tid + kThreads * it, j = e / KT, kk = e % KT;
+                vb[it] = (j < J && kk < kn) ? __ldg(B + j * a.ldb_row + (k0 + kk) * a.ldb_col) : T(0);
+            }
+            __syncthreads();      // the previous tile's readers are done
+#pragma unroll
+            for (int it = 0; it < kLoadsA; ++it) {
+                const int e = tid + kThreads * it;
+                As[e / KT][e % KT] = va[it];
+            }
+#pragma unroll
+            for (int it = 0; it < kLoadsB; ++it) {
+                const int e = tid + kThreads * it;
+                Bs[e / KT][e % KT] = vb[it];
+            }
+            __syncthreads();
+            if (p0 < pairs) {
+#pragma unroll 8
+                for (int kk = 0; kk < KT; ++kk) acc0 = fma(As[m0][kk], Bs[j0][kk], acc0);
+            }
+            if (p1 < pairs) {
+#pragma unroll 8
+                for (int kk = 0; kk < KT; ++kk) acc1 = fma(As[m1][kk], Bs[j1][kk], acc1);
+            }
+        }
+        if (p0 < pairs) ws[(s * M + m0) * J + j0] = acc0;
+        if (p1 < pairs) ws[(s * M + m1) * J + j1] = acc1;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) ttm_splitk_reduce(const TtmArgs a)
 {
@@ -247,8 +319,11 @@ int launch_typed(const TtmPlan& P, const void* A, const void* B, void* C, int ac
         }
         return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
     }
-    if constexpr (sizeof(T) == 4) {
-        // FP32: the 128 x 128 register-tiled kernel of ttm_sgemm.cu
+    if (ttm_skinny(P)) {
+        const int grid = (int)(a.splits < cap ? a.splits : cap);
+        ttm_skinny_kernel<T><<<grid, kThreads, 0, st>>>(a);
+    } else if constexpr (sizeof(T) == 4) {
+        // FP32: the register-tiled kernel of ttm_sgemm.cu
         const int rc = launch_ttm_sgemm(P, A, B, C, accumulate, ws, a.splits, a.kchunk, num_sms, st);
         if (rc != TL_OK) return rc;
     } else {
@@ -266,11 +341,24 @@ int launch_typed(const TtmPlan& P, const void* A, const void* B, void* C, int ac
 
 }  // namespace
 
+bool ttm_skinny(const TtmPlan& P)
+{
+    return P.kernel == K_TTM_SIMT && P.M <= 16 && P.J <= 64 && P.M * P.J <= 512 && P.nq >= 2048;
+}
+
 int64_t ttm_simt_splits(const TtmPlan& P, int num_sms, int64_t* kchunk)
 {
     if (P.kernel == K_TTM_ROWS) {
         if (kchunk) *kchunk = P.nq;
         return 1;
+    }
+    if (ttm_skinny(P)) {
+        // chunks of at least 512 k (whole 64-deep tiles), up to 4 per SM
+        int64_t splits = std::min<int64_t>((P.nq + 511) / 512, (int64_t)num_sms * 4);
+        int64_t kc = (P.nq + splits - 1) / splits;
+        kc = (kc + kSkinnyKT - 1) / kSkinnyKT * kSkinnyKT;
+        if (kchunk) *kchunk = kc;
+        return (P.nq + kc - 1) / kc;
     }
     // split k when the tiles cover less than half of the resident CTAs (one
     // per SM for the FP32 256-thread tiles, four for the FP64 64 x 64 ones)

@@ -73,7 +73,7 @@ __device__ __forceinline__ T reduce_rows(T* v, int sub)
     return r;
 }
 
-template <typename T, int VEC, int L, int R>
+template <typename T, int VEC, int L, int R, bool SPLIT>
 __global__ void __launch_bounds__(kThreads) ttv_row_kernel(const TtvArgs a)
 {
     const T* __restrict__ A = static_cast<const T*>(a.A);
@@ -83,62 +83,77 @@ __global__ void __launch_bounds__(kThreads) ttv_row_kernel(const TtvArgs a)
     const int64_t group = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / L;
     const int64_t ngroups = (int64_t)gridDim.x * kThreads / L;
     const int64_t step = (int64_t)R * ngroups;
-    // every lane of a warp runs the same iterations, so the shuffles always
-    // see a converged warp
-    const int64_t iters = (a.nout + step - 1) / step;
-    for (int s = 0; s < a.splits; ++s) {
-        const int64_t k0 = (int64_t)s * a.kchunk;
-        const int64_t klen = min(a.nq - k0, a.kchunk);
-        for (int64_t it = 0; it < iters; ++it) {
-            int64_t row[R], offA[R];
-            bool ok[R];
-            T acc[R];
+    // Work items are (split, output) pairs, split-major, spread over every
+    // group, so the splits of a long contraction run in parallel; each of a
+    // group's R items in flight has its own k range (SPLIT; without it they
+    // share one and one load of b, at fewer registers).  Every lane of a warp
+    // runs the same iterations, so the shuffles always see a converged warp.
+    const int64_t total = a.nout * (SPLIT ? a.splits : 1);
+    const int64_t iters = (total + step - 1) / step;
+    constexpr bool split = SPLIT;
+    for (int64_t it = 0; it < iters; ++it) {
+        int64_t row[R], offA[R], k0[R], klen[R], sp[R];
+        bool ok[R];
+        T acc[R];
+        int64_t kmax = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t w = (it * R + r) * ngroups + group;
+            ok[r] = w < total;
+            sp[r] = split ? w / a.nout : 0;
+            row[r] = w - sp[r] * a.nout;
+            k0[r] = sp[r] * a.kchunk;
+            klen[r] = ok[r] ? min(a.nq - k0[r], a.kchunk) : 0;
+            kmax = max(kmax, klen[r]);
+            acc[r] = T(0);
+            int64_t off[1] = {0};
+            if (ok[r]) map_offsets<1>(a.out, row[r], 1, off);
+            offA[r] = off[0] + k0[r];
+        }
+        for (int64_t kk = (int64_t)sub * VEC; kk < kmax; kk += (int64_t)L * VEC) {
+            T vb[SPLIT ? R : 1][VEC];
+            if constexpr (!SPLIT) {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) vb[0][v] = __ldg(b + (kk + v) * a.incb);
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v)
+                        vb[r][v] = kk < klen[r] ? __ldg(b + (k0[r] + kk + v) * a.incb) : T(0);
+            }
+            T va[R][VEC];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                row[r] = (it * R + r) * ngroups + group;
-                ok[r] = row[r] < a.nout;
-                acc[r] = T(0);
-                int64_t off[1] = {0};
-                if (ok[r]) map_offsets<1>(a.out, row[r], 1, off);
-                offA[r] = off[0] + k0;
-            }
-            for (int64_t kk = (int64_t)sub * VEC; kk < klen; kk += (int64_t)L * VEC) {
-                T vb[VEC];
+                if (kk < klen[r]) {
+                    vload_stream<T, VEC>(A + offA[r] + kk, va[r]);
+                } else {
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) vb[v] = __ldg(b + (k0 + kk + v) * a.incb);
-                T va[R][VEC];
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (ok[r]) {
-                        vload_stream<T, VEC>(A + offA[r] + kk, va[r]);
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) va[r][v] = T(0);
-                    }
+                    for (int v = 0; v < VEC; ++v) va[r][v] = T(0);
                 }
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) acc[r] = fma(va[r][v], vb[v], acc[r]);
             }
-            const T tot = reduce_rows<T, L, R>(acc, sub);
-            constexpr int kG = L / R;                 // lanes per row after the butterfly
-            if ((sub & (kG - 1)) == 0) {
-                const int rs = sub / kG;
-                int64_t rw = 0;
-                bool okw = false;
 #pragma unroll
-                for (int r = 0; r < R; ++r)
-                    if (r == rs) { rw = row[r]; okw = ok[r]; }
-                if (okw) {
-                    if (a.splits > 1) {
-                        static_cast<T*>(a.ws)[(int64_t)s * a.nout + rw] = tot;
-                    } else {
-                        int64_t off[2];
-                        map_offsets<2>(a.out, rw, 1, off);
-                        T* c = static_cast<T*>(a.C) + off[1];
-                        *c = a.accumulate ? *c + tot : tot;
-                    }
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[r] = fma(va[r][v], vb[SPLIT ? r : 0][v], acc[r]);
+        }
+        const T tot = reduce_rows<T, L, R>(acc, sub);
+        constexpr int kG = L / R;                 // lanes per row after the butterfly
+        if ((sub & (kG - 1)) == 0) {
+            const int rs = sub / kG;
+            int64_t rw = 0, sw = 0;
+            bool okw = false;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (r == rs) { rw = row[r]; sw = sp[r]; okw = ok[r]; }
+            if (okw) {
+                if constexpr (SPLIT) {
+                    static_cast<T*>(a.ws)[sw * a.nout + rw] = tot;
+                } else {
+                    int64_t off[2];
+                    map_offsets<2>(a.out, rw, 1, off);
+                    T* c = static_cast<T*>(a.C) + off[1];
+                    *c = a.accumulate ? *c + tot : tot;
                 }
             }
         }
@@ -376,9 +391,14 @@ int launch_typed(const TtvPlan& P, const void* A, const void* b, void* C, void* 
         return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
     }
     if (P.kernel == K_TTV_ROW) {
-        int64_t threads = (P.nout + 3) / 4 * P.lanes;
+        // one group of `lanes` threads per 4 (split, output) items
+        int64_t threads = (P.nout * P.splits + 3) / 4 * P.lanes;
         int grid = grid_for(threads, num_sms);
-#define TL_ROW(VV, LL) ttv_row_kernel<T, VV, LL, 4><<<grid, kThreads, 0, st>>>(a)
+#define TL_ROW(VV, LL)                                                              \
+    do {                                                                            \
+        if (P.splits > 1) ttv_row_kernel<T, VV, LL, 4, true><<<grid, kThreads, 0, st>>>(a);  \
+        else ttv_row_kernel<T, VV, LL, 4, false><<<grid, kThreads, 0, st>>>(a);            \
+    } while (0)
         if (P.vec == V) {
             switch (P.lanes) {
             case 32: TL_ROW(V, 32); break;

@@ -104,10 +104,12 @@ def test_ttm_full_scale_sampled(tl, cuda_dev, scale_tensors):
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("n,q,J,pi", [((3, 200000), 2, 10, (1, 2)), ((240001, 4), 1, 34, (2, 1)),
-                                      ((5, 30011, 3), 2, 7, (3, 1, 2)), ((2, 70000), 2, 1, (1, 2))])
+                                      ((5, 30011, 3), 2, 7, (3, 1, 2)), ((2, 70000), 2, 1, (1, 2)),
+                                      ((40, 100000), 2, 10, (1, 2)), ((24, 50000, 3), 2, 7, (3, 1, 2))])
 def test_ttm_split_k_long_contraction(tl, cuda_dev, dtype, n, q, J, pi):
     # few rows and a long contraction: the k range is split across CTAs and the
-    # partial sums are added in a fixed order by a second kernel
+    # partial sums are added in a fixed order by a second kernel (the skinny
+    # kernel for at most 16 rows, the tiled kernels above)
     import json
     X = synth.uniform(n, 4400 + J)
     Bm = synth.uniform((J, n[q - 1]), 4401 + J)
@@ -116,12 +118,44 @@ def test_ttm_split_k_long_contraction(tl, cuda_dev, dtype, n, q, J, pi):
     C = torch.empty(int(np.prod(nout)), dtype=TORCH[dtype], device=cuda_dev)
     rc, js = tl.tl_plan_describe(tl.TL_OP_TTM, tl.Desc(A, n, pi), None, q, J, 0, 0,
                                  tl.Desc(C, nout, pi))
-    assert rc == 0 and json.loads(js)["splits"] > 1, js
+    d = json.loads(js)
+    assert rc == 0 and d["splits"] > 1, js
+    M = int(np.prod(n)) // n[q - 1]
+    assert d.get("skinny") == (1 if M <= 16 else None), d
     got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pi, dtype)
     assert rel_err(got, ref) <= TOL[dtype]
     # accumulate through the split path
     C0 = synth.uniform(nout, 4402)
     got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pi, dtype, accumulate=True, C0=C0)
+    assert rel_err(got, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n,q,J,pi,pic,colB", [((1, 2048), 2, 1, (1, 2), (1, 2), False),
+                                               ((16, 100003), 2, 32, (1, 2), (2, 1), False),
+                                               ((7, 4099), 2, 64, (2, 1), (1, 2), True),
+                                               ((2, 3, 60001), 3, 33, (3, 1, 2), (1, 2, 3), True),
+                                               ((5, 9000, 3), 2, 19, (2, 3, 1), (3, 2, 1), False)])
+def test_ttm_skinny_long_contraction(tl, cuda_dev, dtype, n, q, J, pi, pic, colB):
+    # at most 16 rows over n_q >= 2048 (M x J <= 512): the skinny split-K
+    # kernel, with the contraction contiguous in A or strided, B row- or
+    # column-major, C in another layout, a ragged last k tile, one or two
+    # outputs per thread, and accumulation
+    import json
+    X = synth.uniform(n, 4450 + J)
+    Bm = synth.uniform((J, n[q - 1]), 4451 + J)
+    A = put(X, pi, cuda_dev, dtype)
+    nout = tuple(J if r == q - 1 else x for r, x in enumerate(n))
+    C = torch.empty(int(np.prod(nout)), dtype=TORCH[dtype], device=cuda_dev)
+    rc, js = tl.tl_plan_describe(tl.TL_OP_TTM, tl.Desc(A, n, pi), None, q, J, 0, 0,
+                                 tl.Desc(C, nout, pic))
+    d = json.loads(js)
+    assert rc == 0 and d.get("skinny") == 1 and d["splits"] > 1, js
+    got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pic, dtype, col_major=colB)
+    assert rel_err(got, ref) <= TOL[dtype]
+    C0 = synth.uniform(nout, 4452)
+    got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pic, dtype, accumulate=True, C0=C0,
+                        col_major=colB)
     assert rel_err(got, ref) <= TOL[dtype]
 
 

@@ -86,8 +86,8 @@ def test_sgemm_modes_integer_exact_and_real_bounded(tl, cuda_dev, case):
     assert rel_err(got, ref) <= 1e-5
 
 
-@pytest.mark.parametrize("n,q,J,pi", [((3, 200000), 2, 8, (1, 2)), ((240000, 4), 1, 36, (2, 1)),
-                                      ((5, 30011, 3), 2, 7, (3, 1, 2))])
+@pytest.mark.parametrize("n,q,J,pi", [((40, 200000), 2, 8, (1, 2)), ((240000, 20), 1, 36, (2, 1)),
+                                      ((5, 30011, 4), 2, 7, (3, 1, 2))])
 def test_sgemm_split_k_vector_and_element_partials(tl, cuda_dev, n, q, J, pi):
     d = _plan(tl, cuda_dev, n, q, J, pi, pi)
     assert d["splits"] > 1
