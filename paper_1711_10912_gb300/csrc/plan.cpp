@@ -192,7 +192,7 @@ int plan_ttv(const Tensor& A, int64_t incb, uint32_t q, const Tensor& C, TtvPlan
     if (threads < target / 2 && P.nq >= 2 * kmin) {
         int64_t s = (target + threads - 1) / threads;
         s = std::min<int64_t>(s, P.nq / kmin);
-        s = std::min<int64_t>(s, 256);
+        s = std::min<int64_t>(s, 4096);
         if (s > 1) {
             int64_t align = P.kernel == K_TTV_ROW ? (int64_t)P.lanes * P.vec : 4;
             int64_t chunk = (P.nq + s - 1) / s;

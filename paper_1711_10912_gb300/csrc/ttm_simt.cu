@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmArgs a)
 // a CTA stages the M rows of A and the J rows of B in shared memory (every
 // load of the tile issued before the stores) and each thread accumulates one
 // or two (m, j) dot products over ascending k; the partial M x J blocks go
-// to ws[s][m][j] and ttm_splitk_reduce adds them in split order.
+// to ws[s][m][j] and ttm_splitk_reduce adds them.
 constexpr int kSkinnyKT = 64;
 
 template <typename T>
@@ -256,17 +256,30 @@ __global__ void __launch_bounds__(kThreads) ttm_skinny_kernel(const TtmArgs a)
     }
 }
 
-template <typename T>
+// Adds the split partials ws[s][m][j] into C: in split order by one thread
+// per output, or, with WARP (many splits), by a warp per output whose lanes
+// each add every 32nd split in order and combine by a fixed butterfly
+// (deterministic either way).
+template <typename T, bool WARP>
 __global__ void __launch_bounds__(kThreads) ttm_splitk_reduce(const TtmArgs a)
 {
     const T* __restrict__ ws = static_cast<const T*>(a.ws);
     T* __restrict__ C = static_cast<T*>(a.C);
     const int64_t total = a.M * a.J;
-    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * kThreads) {
+    constexpr int kPer = WARP ? 32 : 1;
+    const int lane = threadIdx.x & 31;
+    for (int64_t e = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / kPer; e < total;
+         e += (int64_t)gridDim.x * kThreads / kPer) {
         const int64_t m = e / a.J, j = e - m * a.J;
         T acc = T(0);
-        for (int64_t s = 0; s < a.splits; ++s) acc += ws[s * total + e];
+        if constexpr (WARP) {
+            for (int64_t s = lane; s < a.splits; s += 32) acc += ws[s * total + e];
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+            if (lane != 0) continue;
+        } else {
+            for (int64_t s = 0; s < a.splits; ++s) acc += ws[s * total + e];
+        }
         int64_t off[2];
         map_offsets<2>(a.rows, m, 1, off);
         T* c = C + off[1] + j * a.scq;
@@ -331,10 +344,14 @@ int launch_typed(const TtmPlan& P, const void* A, const void* B, void* C, int ac
         int grid = (int)(work < cap ? work : cap);
         ttm_simt_kernel<T><<<grid, kThreads, 0, st>>>(a);
     }
-    if (a.splits > 1) {
+    if (a.splits >= 64) {
+        int64_t blocks = (P.M * P.J * 32 + kThreads - 1) / kThreads;
+        if (blocks > cap) blocks = cap;
+        ttm_splitk_reduce<T, true><<<(int)blocks, kThreads, 0, st>>>(a);
+    } else if (a.splits > 1) {
         int64_t blocks = (P.M * P.J + kThreads - 1) / kThreads;
         if (blocks > cap) blocks = cap;
-        ttm_splitk_reduce<T><<<(int)blocks, kThreads, 0, st>>>(a);
+        ttm_splitk_reduce<T, false><<<(int)blocks, kThreads, 0, st>>>(a);
     }
     return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
 }

@@ -322,15 +322,27 @@ __global__ void __launch_bounds__(kThreads) ttv_col_kernel(const TtvArgs a)
     }
 }
 
-// Adds the split partial sums ws[s][e] in split order and writes C.
-template <typename T>
+// Adds the split partial sums ws[s][e] and writes C: in split order by one
+// thread per output, or, with WARP (many splits), by a warp per output whose
+// lanes each add every 32nd split in order and combine by a fixed butterfly
+// (deterministic either way).
+template <typename T, bool WARP>
 __global__ void __launch_bounds__(kThreads) ttv_splitk_reduce(const TtvArgs a)
 {
     const T* ws = static_cast<const T*>(a.ws);
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < a.nout; e += stride) {
+    constexpr int kPer = WARP ? 32 : 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * kThreads / kPer;
+    for (int64_t e = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / kPer; e < a.nout; e += stride) {
         T sum = T(0);
-        for (int s = 0; s < a.splits; ++s) sum += ws[(int64_t)s * a.nout + e];
+        if constexpr (WARP) {
+            for (int s = lane; s < a.splits; s += 32) sum += ws[(int64_t)s * a.nout + e];
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, m);
+            if (lane != 0) continue;
+        } else {
+            for (int s = 0; s < a.splits; ++s) sum += ws[(int64_t)s * a.nout + e];
+        }
         int64_t off[2];
         map_offsets<2>(a.out, e, 1, off);
         T* c = static_cast<T*>(a.C) + off[1];
@@ -421,8 +433,10 @@ int launch_typed(const TtvPlan& P, const void* A, const void* b, void* C, void* 
         if (P.vec == V) ttv_col_kernel<T, V, 4><<<grid, kThreads, 0, st>>>(a);
         else ttv_col_kernel<T, 1, 4><<<grid, kThreads, 0, st>>>(a);
     }
-    if (P.splits > 1) {
-        ttv_splitk_reduce<T><<<grid_for(P.nout, num_sms), kThreads, 0, st>>>(a);
+    if (P.splits >= 64) {
+        ttv_splitk_reduce<T, true><<<grid_for(P.nout * 32, num_sms), kThreads, 0, st>>>(a);
+    } else if (P.splits > 1) {
+        ttv_splitk_reduce<T, false><<<grid_for(P.nout, num_sms), kThreads, 0, st>>>(a);
     }
     return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
 }
