@@ -157,7 +157,12 @@ __global__ void __launch_bounds__(kThreads) ew_flat_kernel(const EwArgs a)
     }
 }
 
-template <typename T>
+// Any strides: each element's offsets come from the layout function, with
+// multiply-high division and (ND > 0) the collapsed dim count known at
+// compile time, so the decode unrolls; U elements per thread (kThreads
+// apart: C's writes stay contiguous along dim 0), all loads before the
+// stores, one such chunk per thread.
+template <typename T, int ND, int U>
 __global__ void __launch_bounds__(kThreads) ew_generic_kernel(const EwArgs a)
 {
     const T* __restrict__ A = static_cast<const T*>(a.A);
@@ -165,13 +170,25 @@ __global__ void __launch_bounds__(kThreads) ew_generic_kernel(const EwArgs a)
     T* __restrict__ C = static_cast<T*>(a.C);
     const T alpha = (T)a.alpha;
     const bool unary = (a.op == TL_COPY || a.op == TL_SCALE);
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < a.N; e += stride) {
-        int64_t off[3];
-        map_offsets<3>(a.sp, e, 1, off);
-        T x = __ldg(A + off[0]);
-        T y = unary ? T(0) : __ldg(B + off[1]);
-        C[off[2]] = apply<T>(a.op, x, y, alpha);
+    const int64_t step = (int64_t)gridDim.x * kThreads * U;
+    for (int64_t g0 = (int64_t)blockIdx.x * kThreads * U + threadIdx.x; g0 < a.N; g0 += step) {
+        int64_t off[U][3];
+        T x[U], y[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t e = g0 + (int64_t)u * kThreads;
+            if (e < a.N) {
+                if constexpr (ND > 0) map_offsets_nd<ND, 3>(a.sp, a.dv, e, 1, off[u]);
+                else map_offsets_fast<3>(a.sp, a.dv, e, 1, off[u]);
+                x[u] = __ldg(A + off[u][0]);
+                y[u] = unary ? T(0) : __ldg(B + off[u][1]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t e = g0 + (int64_t)u * kThreads;
+            if (e < a.N) C[off[u][2]] = apply<T>(a.op, x[u], y[u], alpha);
+        }
     }
 }
 
@@ -479,14 +496,6 @@ int tile_edge(int64_t n)
     return (int)(ts < tb ? small : big);
 }
 
-int grid_for(int64_t threads, int num_sms)
-{
-    int64_t blocks = (threads + kThreads - 1) / kThreads;
-    int64_t cap = (int64_t)num_sms * (2048 / kThreads);
-    if (blocks > cap) blocks = cap;
-    return (int)(blocks < 1 ? 1 : blocks);
-}
-
 template <typename T>
 int launch_typed(const EwPlan& P, const void* A, const void* B, double alpha, void* C,
                  int num_sms, cudaStream_t st)
@@ -565,7 +574,18 @@ int launch_typed(const EwPlan& P, const void* A, const void* B, double alpha, vo
         default: ew_rows_kernel<T, V, U, 0><<<grid, kThreads, 0, st>>>(a); break;
         }
     } else {
-        ew_generic_kernel<T><<<grid_for(P.N, num_sms), kThreads, 0, st>>>(a);
+        a.dv = make_devdiv(P.sp, 1);
+        const int grid = chunk_grid(P.N);
+        switch (a.sp.small ? P.sp.nd : 0) {
+        case 1: ew_generic_kernel<T, 1, U><<<grid, kThreads, 0, st>>>(a); break;
+        case 2: ew_generic_kernel<T, 2, U><<<grid, kThreads, 0, st>>>(a); break;
+        case 3: ew_generic_kernel<T, 3, U><<<grid, kThreads, 0, st>>>(a); break;
+        case 4: ew_generic_kernel<T, 4, U><<<grid, kThreads, 0, st>>>(a); break;
+        case 5: ew_generic_kernel<T, 5, U><<<grid, kThreads, 0, st>>>(a); break;
+        case 6: ew_generic_kernel<T, 6, U><<<grid, kThreads, 0, st>>>(a); break;
+        case 7: ew_generic_kernel<T, 7, U><<<grid, kThreads, 0, st>>>(a); break;
+        default: ew_generic_kernel<T, 0, U><<<grid, kThreads, 0, st>>>(a); break;
+        }
     }
     return cudaGetLastError() == cudaSuccess ? TL_OK : TL_ECUDA;
 }

@@ -52,12 +52,6 @@ struct Desc {
         t.data = data;
         return t;
     }
-    int64_t count() const
-    {
-        int64_t c = 1;
-        for (int64_t x : n) c *= x;
-        return c;
-    }
 };
 
 // Layout tuple of A's strides (modes ordered by increasing stride).

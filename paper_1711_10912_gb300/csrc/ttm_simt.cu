@@ -130,7 +130,10 @@ __global__ void __launch_bounds__(kThreads) ttm_simt_kernel(const TtmArgs a)
 // alone fill the GPU, down to 1 for few rows, so small problems still use
 // every SM); its outputs are accumulated in registers, k streams in groups of
 // 8 loads, B is read as shared-memory broadcasts.  Rows are contiguous in C
-// whenever j is not.
+// whenever j is not: then the items are numbered row-fastest, so a warp's 32
+// threads write 32 consecutive rows of one column (128 bytes for FP32) instead
+// of 8 rows of four column groups; when j is contiguous in C the threads of a
+// row stay together.
 template <typename T, int JB>
 __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmArgs a)
 {
@@ -150,8 +153,16 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmArgs a)
     const int64_t items = a.M * groups;
     for (int64_t it = (int64_t)blockIdx.x * kThreads + threadIdx.x; it < items;
          it += (int64_t)gridDim.x * kThreads) {
-        const int64_t m = it / groups;
-        const int j0 = (int)(it - m * groups) * JB;
+        int64_t m;
+        int j0;
+        if (a.scq != 1) {
+            const int64_t g = it / a.M;
+            m = it - g * a.M;
+            j0 = (int)g * JB;
+        } else {
+            m = it / groups;
+            j0 = (int)(it - m * groups) * JB;
+        }
         int64_t off[2];
         map_offsets<2>(a.rows, m, 1, off);
         const T* pa = A + off[0];
