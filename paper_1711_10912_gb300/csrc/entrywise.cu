@@ -238,74 +238,63 @@ __global__ void __launch_bounds__(kThreads) ew_rows_kernel(const EwArgs a)
     }
 }
 
-// Tile over dims 0 (fastest in C) and t.  Block = 32 x 8 threads; each
-// thread handles 4 rows of the 32 x 32 tile in each phase.
-constexpr int kTile = 32;
+// Tile over dims 0 (fastest in C) and t with element accesses, for extents
+// or strides that rule out 16-byte vectors: a T0 x TT tile of 1024 elements
+// (16 x 64, 32 x 32, 64 x 16 or 128 x 8, whichever the ragged edges fill
+// best: an extent of 9 along t fills a 128 x 8 tile's rows at 9 / 16 instead
+// of 9 / 32), 256 threads with 4 elements each per phase, one tile per CTA.
+// Staged inputs (faster along t) are read with lanes along t into a padded
+// [dim 0][t] shared tile; C and direct inputs go along dim 0.
+constexpr int kTileElems = 1024;
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) ew_tile_kernel(const EwArgs a, int64_t tiles0,
-                                                           int64_t tiles1, int64_t batch)
+template <typename T, int T0>
+__global__ void __launch_bounds__(kThreads) ew_tile_kernel(const EwArgs a, int64_t total)
 {
-    __shared__ T tA[kTile][kTile + 1];
-    __shared__ T tB[kTile][kTile + 1];
+    constexpr int TT = kTileElems / T0;
+    __shared__ T tA[T0][TT + 1];
+    __shared__ T tB[T0][TT + 1];
     const T* __restrict__ A = static_cast<const T*>(a.A);
     const T* __restrict__ B = static_cast<const T*>(a.B);
     T* __restrict__ C = static_cast<T*>(a.C);
     const T alpha = (T)a.alpha;
     const bool unary = (a.op == TL_COPY || a.op == TL_SCALE);
     const int t = a.tdim;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int64_t n0 = a.sp.n[0], nt = a.sp.n[t];
     // an input is staged when dim t is its faster dim of the two
     const bool stageA = a.sp.s[0][t] < a.sp.s[0][0];
     const bool stageB = !unary && a.sp.s[1][t] < a.sp.s[1][0];
-    const int64_t total = tiles0 * tiles1 * batch;
+    const int lt = threadIdx.x % TT, lr = threadIdx.x / TT;     // load phase
+    const int lx = threadIdx.x % T0, ly = threadIdx.x / T0;     // write phase
     for (int64_t blk = blockIdx.x; blk < total; blk += gridDim.x) {
-        int64_t bt0 = blk % tiles0;
-        int64_t rest = blk / tiles0;
-        int64_t bt1 = rest % tiles1;
-        int64_t bz = rest / tiles1;
-        // base offsets of the batch index over the remaining dims
-        int64_t base[3] = {0, 0, 0};
-        {
-            int64_t g = bz;
-            for (int d = 1; d < a.sp.nd; ++d) {
-                if (d == t) continue;
-                int64_t i = g % a.sp.n[d];
-                g /= a.sp.n[d];
-#pragma unroll
-                for (int o = 0; o < 3; ++o) base[o] += i * a.sp.s[o][d];
-            }
-        }
-        const int64_t i0b = bt0 * kTile, itb = bt1 * kTile;
-        __syncthreads();
-        // load phase: lanes run along dim t
+        int64_t bt0, bt1, base[3];
+        tile_decode<-1>(a, blk, bt0, bt1, base);
+        const int64_t i0b = bt0 * T0, itb = bt1 * TT;
+        __syncthreads();          // the previous tile's readers are done
         if (stageA || stageB) {
 #pragma unroll
-            for (int r = 0; r < kTile; r += 8) {
-                int64_t i0 = i0b + ty + r, it = itb + tx;
+            for (int r = 0; r < T0; r += kThreads / TT) {
+                const int64_t i0 = i0b + lr + r, it = itb + lt;
                 if (i0 < n0 && it < nt) {
                     if (stageA)
-                        tA[ty + r][tx] = __ldcs(A + checked_off(a.sp, 0, base[0] + i0 * a.sp.s[0][0] +
+                        tA[lr + r][lt] = __ldcs(A + checked_off(a.sp, 0, base[0] + i0 * a.sp.s[0][0] +
                                                                      it * a.sp.s[0][t], 1));
                     if (stageB)
-                        tB[ty + r][tx] = __ldcs(B + checked_off(a.sp, 1, base[1] + i0 * a.sp.s[1][0] +
+                        tB[lr + r][lt] = __ldcs(B + checked_off(a.sp, 1, base[1] + i0 * a.sp.s[1][0] +
                                                                      it * a.sp.s[1][t], 1));
                 }
             }
         }
         __syncthreads();
-        // write phase: lanes run along dim 0
 #pragma unroll
-        for (int r = 0; r < kTile; r += 8) {
-            int64_t i0 = i0b + tx, it = itb + ty + r;
+        for (int r = 0; r < TT; r += kThreads / T0) {
+            const int64_t i0 = i0b + lx, it = itb + ly + r;
             if (i0 < n0 && it < nt) {
-                T x = stageA ? tA[tx][ty + r]
+                T x = stageA ? tA[lx][ly + r]
                              : __ldcs(A + checked_off(a.sp, 0, base[0] + i0 * a.sp.s[0][0] +
                                                                    it * a.sp.s[0][t], 1));
                 T y = T(0);
                 if (!unary)
-                    y = stageB ? tB[tx][ty + r]
+                    y = stageB ? tB[lx][ly + r]
                                : __ldcs(B + checked_off(a.sp, 1, base[1] + i0 * a.sp.s[1][0] +
                                                                      it * a.sp.s[1][t], 1));
                 C[checked_off(a.sp, 2, base[2] + i0 * a.sp.s[2][0] + it * a.sp.s[2][t], 1)] =
@@ -485,6 +474,24 @@ void launch_tile_vec_nb(int nb, int vkind, int grid, size_t smem, cudaStream_t s
     }
 }
 
+// Dim-0 edge of the element tile kernel's T0 x (1024 / T0) tile: the shape
+// (16 x 64, 32 x 32, 64 x 16 or 128 x 8) whose ragged edges leave the fewest
+// idle slots, 32 x 32 on ties.
+int scalar_tile_t0(int64_t n0, int64_t nt)
+{
+    auto fill = [](int64_t n, int64_t e) { return (double)n / (double)((n + e - 1) / e * e); };
+    int best = 32;
+    double bf = fill(n0, 32) * fill(nt, 32);
+    for (int t0 : {16, 64, 128}) {
+        const double f = fill(n0, t0) * fill(nt, kTileElems / t0);
+        if (f > bf + 1e-9) {
+            bf = f;
+            best = t0;
+        }
+    }
+    return best;
+}
+
 // Tile edge (elements) along one dim: 256 bytes, or 128 when that fills the
 // ragged last tile better (an extent of 96 FP32 elements: three 32-element
 // tiles instead of two of 64, the second half empty).
@@ -523,13 +530,14 @@ int launch_typed(const EwPlan& P, const void* A, const void* B, double alpha, vo
         const bool sa = P.sp.d[P.tdim].s[0] < P.sp.d[0].s[0];
         const bool sb = !unary && P.sp.d[P.tdim].s[1] < P.sp.d[0].s[1];
         const bool vec = P.vec > 1 && (sa || sb);
-        const int t0 = vec ? tile_edge<T>(P.sp.d[0].n) : kTile;
-        const int tt = vec ? tile_edge<T>(P.sp.d[P.tdim].n) : kTile;
+        const int st0 = scalar_tile_t0(P.sp.d[0].n, P.sp.d[P.tdim].n);
+        const int t0 = vec ? tile_edge<T>(P.sp.d[0].n) : st0;
+        const int tt = vec ? tile_edge<T>(P.sp.d[P.tdim].n) : kTileElems / st0;
         int64_t tiles0 = (P.sp.d[0].n + t0 - 1) / t0;
         int64_t tiles1 = (P.sp.d[P.tdim].n + tt - 1) / tt;
         int64_t batch = P.N / (P.sp.d[0].n * P.sp.d[P.tdim].n);
         int64_t total = tiles0 * tiles1 * batch;
-        if (vec) {
+        {
             // tile decode tables: tiles along dim 0 and t, then the batch dims
             a.ntile0 = (uint32_t)tiles0;
             a.ntile1 = (uint32_t)tiles1;
@@ -546,10 +554,12 @@ int launch_typed(const EwPlan& P, const void* A, const void* B, double alpha, vo
             }
             if (!a.idx32 && (tiles0 >= (int64_t(1) << 32) || tiles1 >= (int64_t(1) << 32)))
                 return TL_EUNSUPPORTED;
+        }
+        const int grid = (int)(total < INT32_MAX ? total : INT32_MAX);
+        if (vec) {
             // one tile per CTA; an input is staged when dim t is its faster
             // dim of the two (the planner's vector conditions make it unit
             // stride there)
-            const int grid = (int)(total < INT32_MAX ? total : INT32_MAX);
             const size_t smem = (size_t)((sa ? 1 : 0) + (sb ? 1 : 0)) * t0 * (tt + 1) * sizeof(T);
             const int vkind = unary ? 0 : (sa && sb) ? 1 : sa ? 2 : 3;
             const int nb = a.idx32 ? a.nb : -1;
@@ -559,9 +569,12 @@ int launch_typed(const EwPlan& P, const void* A, const void* B, double alpha, vo
             else if (tt == B) launch_tile_vec_nb<T, S, B>(nb, vkind, grid, smem, st, a, total);
             else launch_tile_vec_nb<T, S, S>(nb, vkind, grid, smem, st, a, total);
         } else {
-            const int64_t cap = (int64_t)num_sms * 8;
-            const int grid = (int)(total < cap ? total : cap);
-            ew_tile_kernel<T><<<grid, kThreads, 0, st>>>(a, tiles0, tiles1, batch);
+            switch (st0) {
+            case 16: ew_tile_kernel<T, 16><<<grid, kThreads, 0, st>>>(a, total); break;
+            case 64: ew_tile_kernel<T, 64><<<grid, kThreads, 0, st>>>(a, total); break;
+            case 128: ew_tile_kernel<T, 128><<<grid, kThreads, 0, st>>>(a, total); break;
+            default: ew_tile_kernel<T, 32><<<grid, kThreads, 0, st>>>(a, total); break;
+            }
         }
     } else if (P.kernel == K_EW_ROWS) {
         a.dv = make_devdiv(P.sp, V);

@@ -352,12 +352,15 @@ int plan_entrywise(int32_t op, const Tensor& A, const Tensor* B, const Tensor& C
             P.vec = V;
         }
     }
-    // Tiles over (dim 0, dim t) with both extents far below the 32-element
-    // tile edge would leave most threads idle (high-order tensors with small
+    // Tiles over (dim 0, dim t) of 1024 elements (16 x 64 .. 128 x 8) that
+    // even the best shape leaves mostly idle (high-order tensors with small
     // extents): map every element instead.
     if (P.kernel == K_EW_TILE) {
-        auto fill = [](int64_t n) { return (double)n / (double)((n + 31) / 32 * 32); };
-        if (fill(P.sp.d[0].n) * fill(P.sp.d[P.tdim].n) < 0.2) {
+        auto fill = [](int64_t n, int64_t e) { return (double)n / (double)((n + e - 1) / e * e); };
+        double best = 0.0;
+        for (int64_t t0 : {16, 32, 64, 128})
+            best = std::max(best, fill(P.sp.d[0].n, t0) * fill(P.sp.d[P.tdim].n, 1024 / t0));
+        if (best < 0.2) {
             P.kernel = K_EW_GENERIC;
             P.vec = 1;
             P.tdim = -1;

@@ -140,6 +140,34 @@ def test_entrywise_vector_tile_path_bit_exact(tl, cuda_dev, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("shape,pa,pb,pc", [((7, 3001), (1, 2), (2, 1), (2, 1)),
+                                            ((3001, 9), (2, 1), (1, 2), (1, 2)),
+                                            ((7, 1001, 5), (2, 3, 1), (3, 2, 1), (1, 2, 3)),
+                                            ((33, 31, 6), (1, 2, 3), (2, 1, 3), (1, 2, 3)),
+                                            ((13, 4097), (1, 2), (2, 1), (2, 1))])
+def test_entrywise_element_tiles_bit_exact(tl, cuda_dev, dtype, shape, pa, pb, pc):
+    # odd extents rule out 16-byte vectors: the element tile kernel, whose
+    # 1024-element tile takes the shape (16 x 64 .. 128 x 8) that the ragged
+    # edges fill best; binary and unary operations, one or both inputs staged
+    import json
+    X = synth.normal(shape, 3560, dtype=np.float64)
+    Y = synth.normal(shape, 3561, dtype=np.float64) + 3.0
+    for op in ("add", "div", "copy"):
+        A = put(X, pa, cuda_dev, dtype)
+        B = put(Y, pb, cuda_dev, dtype)
+        C = torch.empty_like(A)
+        unary = OPS[op] in (4, 5)
+        rc, js = tl.tl_plan_describe(tl.TL_OP_ENTRYWISE, tl.Desc(A, shape, pa),
+                                     None if unary else tl.Desc(B, shape, pb), 0, 0, 0, OPS[op],
+                                     tl.Desc(C, shape, pc))
+        P = json.loads(js)
+        if not (unary and pa == pc):
+            assert P["kernel"] == "ew_tile" and P["vec"] == 1, P
+        got, ref = ew_case(tl, cuda_dev, OPS[op], X, Y, pa, pb, pc, dtype)
+        np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_entrywise_shared_fastest_mode_rows_path(tl, cuda_dev, dtype):
     # same fastest mode, the other modes permuted: the per-vector mapper path
     import json
