@@ -32,6 +32,9 @@ struct TtmArgs {
     const void* B;
     void* C;
     DevSpace rows;      // operands 0 = A, 1 = C
+    DevDiv rdiv;        // ttm_rows: division by the row extents
+    int idx32;          // ttm_rows: item indices fit in 31 bits
+    FastDiv fdM, fdG;   // ttm_rows: division by M and by the column groups
     int64_t M, J, nq, saq, scq, ldb_row, ldb_col;
     int64_t tiles_m, tiles_j;
     int accumulate;
@@ -155,7 +158,18 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmArgs a)
          it += (int64_t)gridDim.x * kThreads) {
         int64_t m;
         int j0;
-        if (a.scq != 1) {
+        if (a.idx32) {
+            const uint32_t u = (uint32_t)it;
+            if (a.scq != 1) {
+                const uint32_t g = fast_div(u, a.fdM);
+                m = u - g * (uint32_t)a.M;
+                j0 = (int)g * JB;
+            } else {
+                const uint32_t mm = fast_div(u, a.fdG);
+                m = mm;
+                j0 = (int)(u - mm * (uint32_t)groups) * JB;
+            }
+        } else if (a.scq != 1) {
             const int64_t g = it / a.M;
             m = it - g * a.M;
             j0 = (int)g * JB;
@@ -164,7 +178,7 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmArgs a)
             j0 = (int)(it - m * groups) * JB;
         }
         int64_t off[2];
-        map_offsets<2>(a.rows, m, 1, off);
+        map_offsets_fast<2>(a.rows, a.rdiv, m, 1, off);
         const T* pa = A + off[0];
         T* pc = C + off[1];
         T acc[JB];
@@ -324,6 +338,7 @@ int launch_typed(const TtmPlan& P, const void* A, const void* B, void* C, int ac
     if (a.splits > 1 && !ws) return TL_ENOMEM;
     int64_t cap = (int64_t)num_sms * 4;
     if (P.kernel == K_TTM_ROWS) {
+        a.rdiv = make_devdiv(P.rows, 1);
         // columns per work item: as many as keep at least two CTAs per SM busy
         const int64_t want = (int64_t)num_sms * 2 * kThreads;
         int jb = 16;
@@ -331,6 +346,9 @@ int launch_typed(const TtmPlan& P, const void* A, const void* B, void* C, int ac
         const int Jp = (int)((P.J + jb - 1) / jb * jb);
         const size_t smem = (size_t)P.nq * Jp * sizeof(T);
         const int64_t items = P.M * (Jp / jb);
+        a.idx32 = items < (int64_t(1) << 31) ? 1 : 0;
+        a.fdM = make_fastdiv(a.idx32 ? (uint32_t)P.M : 1u);
+        a.fdG = make_fastdiv((uint32_t)(Jp / jb));
         int64_t blocks = (items + kThreads - 1) / kThreads;
         const int64_t rcap = (int64_t)num_sms * 8;
         if (blocks > rcap) blocks = rcap;
