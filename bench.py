@@ -61,7 +61,8 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=1 << 18,
                     help="outputs per ttv/ttm op in the CPU-oracle sample")
     ap.add_argument("--profile-case", default=None,
-                    choices=["ttm_tc_x64", "sgemm_384", "batch_512", "ew_add_128x48"],
+                    choices=["ttm_tc_x64", "sgemm_384", "batch_512", "ew_add_128x48",
+                             "ttm_rows_q1", "tucker_512"],
                     help="run one small case three times and exit (the workloads the ncu "
                          "captures under profiles/ use; no JSON line)")
     ap.add_argument("--no-batch", action="store_true")
@@ -518,7 +519,10 @@ def profile_case(name):
     launch (default unit choices); ew_add_128x48 = the first-order +
     last-order add of two 128 x 48 x 128 x 128 FP32 tensors (0.4 GB each: the
     vector tile kernel with the 64 x 64 tiles and two batch dims of the
-    128^4 add)."""
+    128^4 add); ttm_rows_q1 = FP32 ttm of a 2 x 2 x 2 x 4 x 14 x 575 x 34
+    tensor (layout (5, 3, 4, 6, 7, 1, 2)) by a 35 x 2 matrix along mode 1 (an
+    output-heavy row contraction: 35 MB read, 0.61 GB written); tucker_512 =
+    the 512^3 -> 64^3 projection in one split-BF16x3 tl_ttms call."""
     import torch
     import synth
     from paper_1711_10912_gb300 import build as tlbuild
@@ -545,6 +549,23 @@ def profile_case(name):
         tl.check(rc)
         keep.append(batch)
         fn = lambda: tl.check(tl.tl_batch_run(batch, sh))
+    elif name == "ttm_rows_q1":
+        n, pi, J = (2, 2, 2, 4, 14, 575, 34), (5, 3, 4, 6, 7, 1, 2), 35
+        N = int(np.prod(n))
+        A = synth.device_normal(torch, N, 71_004, torch.float32, dev)
+        B = synth.device_normal(torch, J * n[0], 71_005, torch.float32, dev)
+        C = torch.empty(N // n[0] * J, dtype=torch.float32, device=dev)
+        DA, DC = tl.Desc(A, n, pi), tl.Desc(C, (J,) + n[1:], pi)
+        fn = lambda: tl.check(tl.tl_ttm(DA, B, J, n[0], 1, 1, DC, tl.TL_P_F32, 0, sh))
+    elif name == "tucker_512":
+        n3, mem, _, _, U = synth.precision_case()
+        A = torch.from_numpy(mem).to(dev)
+        Ud = [torch.from_numpy(np.ascontiguousarray(u).reshape(-1)).to(dev) for u in U]
+        r = U[0].shape[0]
+        C = torch.empty(r ** 3, dtype=torch.float32, device=dev)
+        keep.append(Ud)
+        fn = lambda: tl.check(tl.tl_ttms(tl.Desc(A, n3), Ud, (r,) * 3, (1, 2, 3),
+                                         tl.Desc(C, (r,) * 3), tl.TL_P_BF16X3, sh))
     else:
         n = (128, 48, 128, 128)
         N = 128 ** 3 * 48

@@ -310,14 +310,13 @@ __device__ void unit_ttm(const BOp& op, int64_t m0, uint8_t* smem)
 // FP32, J <= 32 for FP64): one row of A per thread, JB <= 16 of its outputs
 // kept in registers per pass (further passes re-read the row, from L1/L2,
 // when J > 16: on the 4096-operation batch recipe that ran the small ttm
-// operations in 1.69 ms against 1.84 with 32 columns per pass), k unrolled 8
-// deep so eight loads of A are in flight per thread, B read as 16-byte
-// broadcasts.
+// operations in 1.69 ms against 1.84 with 32 columns per pass), the row's
+// loads issued in chunks of 8 and a remainder chunk of exact length (row_dot)
+// so that a short contraction waits for one memory latency, B read as
+// 16-byte broadcasts.
 template <typename T, int JB>
 __device__ void unit_ttm_small(const BOp& op, int64_t e0, int64_t e1, uint8_t* smem)
 {
-    constexpr int V = 16 / sizeof(T);
-    using VT = typename Vec<T, V>::type;
     const T* A = static_cast<const T*>(op.A);
     const T* B = static_cast<const T*>(op.B);
     T* C = static_cast<T*>(op.C);
@@ -338,40 +337,18 @@ __device__ void unit_ttm_small(const BOp& op, int64_t e0, int64_t e1, uint8_t* s
             T acc[JB];
 #pragma unroll
             for (int j = 0; j < JB; ++j) acc[j] = T(0);
-            int k = 0;
-            for (; k + 8 <= nq; k += 8) {
-                T a[8];
+            row_dot<T, JB>(pa, op.saq, nq, Bs + j0, JT, acc);
+            T* pj = pc + (int64_t)j0 * op.scq;
+            if (!op.accumulate && j0 + JB <= J) {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) a[u] = __ldg(pa + (int64_t)(k + u) * op.saq);
+                for (int j = 0; j < JB; ++j) pj[(int64_t)j * op.scq] = acc[j];
+            } else {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const VT* brow = reinterpret_cast<const VT*>(Bs + (k + u) * JT + j0);
-#pragma unroll
-                    for (int j = 0; j < JB / V; ++j) {
-                        const VT bv = brow[j];
-                        const T* be = reinterpret_cast<const T*>(&bv);
-#pragma unroll
-                        for (int v = 0; v < V; ++v)
-                            acc[j * V + v] = fma(a[u], be[v], acc[j * V + v]);
+                for (int j = 0; j < JB; ++j) {
+                    if (j0 + j < J) {
+                        T* p = pj + (int64_t)j * op.scq;
+                        *p = op.accumulate ? *p + acc[j] : acc[j];
                     }
-                }
-            }
-            for (; k < nq; ++k) {
-                const T a = __ldg(pa + (int64_t)k * op.saq);
-                const VT* brow = reinterpret_cast<const VT*>(Bs + k * JT + j0);
-#pragma unroll
-                for (int j = 0; j < JB / V; ++j) {
-                    const VT bv = brow[j];
-                    const T* be = reinterpret_cast<const T*>(&bv);
-#pragma unroll
-                    for (int v = 0; v < V; ++v) acc[j * V + v] = fma(a, be[v], acc[j * V + v]);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < JB; ++j) {
-                if (j0 + j < J) {
-                    T* p = pc + (int64_t)(j0 + j) * op.scq;
-                    *p = op.accumulate ? *p + acc[j] : acc[j];
                 }
             }
         }

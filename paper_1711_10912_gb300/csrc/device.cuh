@@ -289,4 +289,60 @@ __device__ __forceinline__ void vstore(T* p, const T* r)
     }
 }
 
+// One row of a row-by-matrix product (Eq. 25 with n_q small): acc[j] +=
+// sum over u < NQ of a[u * sa] * b[u * ldb + j], u ascending.  All NQ loads
+// of the row are issued before the first product, so a short contraction
+// waits for one memory latency rather than NQ of them.
+template <typename T, int JB, int NQ>
+__device__ __forceinline__ void row_chunk(const T* __restrict__ a, int64_t sa, const T* b, int ldb,
+                                          T* acc)
+{
+    T x[NQ];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) x[u] = __ldg(a + (int64_t)u * sa);
+    // b's rows start at multiples of JB elements from a 16-byte aligned
+    // base: 16-byte reads where JB elements fill whole vectors
+    constexpr int V = 16 / (int)sizeof(T);
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+        if constexpr (JB % V == 0) {
+            using VT = typename Vec<T, V>::type;
+            const VT* br = reinterpret_cast<const VT*>(b + u * ldb);
+#pragma unroll
+            for (int c = 0; c < JB / V; ++c) {
+                const VT v = br[c];
+                const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+                for (int i = 0; i < V; ++i) acc[c * V + i] = fma(x[u], e[i], acc[c * V + i]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < JB; ++j) acc[j] = fma(x[u], b[u * ldb + j], acc[j]);
+        }
+    }
+}
+
+// The whole contraction of one row: chunks of 8, then the remainder as one
+// chunk of its exact length (a warp-uniform branch on n_q).
+template <typename T, int JB>
+__device__ __forceinline__ void row_dot(const T* __restrict__ a, int64_t sa, int nq, const T* b,
+                                        int ldb, T* acc)
+{
+    const int k8 = nq & ~7;
+    for (int k0 = 0; k0 < k8; k0 += 8)
+        row_chunk<T, JB, 8>(a + (int64_t)k0 * sa, sa, b + k0 * ldb, ldb, acc);
+    const T* at = a + (int64_t)k8 * sa;
+    const T* bt = b + k8 * ldb;
+    switch (nq - k8) {
+    case 1: row_chunk<T, JB, 1>(at, sa, bt, ldb, acc); break;
+    case 2: row_chunk<T, JB, 2>(at, sa, bt, ldb, acc); break;
+    case 3: row_chunk<T, JB, 3>(at, sa, bt, ldb, acc); break;
+    case 4: row_chunk<T, JB, 4>(at, sa, bt, ldb, acc); break;
+    case 5: row_chunk<T, JB, 5>(at, sa, bt, ldb, acc); break;
+    case 6: row_chunk<T, JB, 6>(at, sa, bt, ldb, acc); break;
+    case 7: row_chunk<T, JB, 7>(at, sa, bt, ldb, acc); break;
+    default: break;
+    }
+}
+
 }  // namespace tl

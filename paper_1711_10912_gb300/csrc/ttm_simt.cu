@@ -184,25 +184,18 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmArgs a)
         T acc[JB];
 #pragma unroll
         for (int j = 0; j < JB; ++j) acc[j] = T(0);
-        for (int k0 = 0; k0 < nq; k0 += 8) {
-            T x[8];
+        row_dot<T, JB>(pa, a.saq, nq, Bs + j0, Jp, acc);
+        pc += (int64_t)j0 * a.scq;
+        if (!a.accumulate && j0 + JB <= J) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                x[u] = k0 + u < nq ? __ldg(pa + (int64_t)(k0 + u) * a.saq) : T(0);
+            for (int j = 0; j < JB; ++j) pc[(int64_t)j * a.scq] = acc[j];
+        } else {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (k0 + u < nq) {
-                    const T* br = Bs + (k0 + u) * Jp + j0;
-#pragma unroll
-                    for (int j = 0; j < JB; ++j) acc[j] = fma(x[u], br[j], acc[j]);
+            for (int j = 0; j < JB; ++j) {
+                if (j0 + j < J) {
+                    T* c = pc + (int64_t)j * a.scq;
+                    *c = a.accumulate ? *c + acc[j] : acc[j];
                 }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < JB; ++j) {
-            if (j0 + j < J) {
-                T* c = pc + (int64_t)(j0 + j) * a.scq;
-                *c = a.accumulate ? *c + acc[j] : acc[j];
             }
         }
     }

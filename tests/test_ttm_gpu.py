@@ -182,3 +182,31 @@ def test_ttm_rows_short_contractions(tl, cuda_dev, dtype, n, q, J, pi, pic):
     C0 = synth.uniform(nout, 4502)
     got, ref = ttm_case(tl, cuda_dev, X, q, Bm, pi, pic, dtype, accumulate=True, C0=C0)
     assert rel_err(got, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("nq", [1, 2, 3, 4, 5, 6, 7, 8, 13, 16, 17])
+def test_ttm_rows_every_contraction_remainder(tl, cuda_dev, dtype, nq):
+    # the row kernel loads a row in chunks of 8 and a remainder chunk of its
+    # exact length: every remainder, alone and after whole chunks, with J
+    # spanning two full 16-column groups and a ragged one (27331 rows are
+    # enough items for 16 columns per item), the contracted mode neither
+    # first nor last in memory; integer inputs make every sum exact, so the
+    # result is bit-exact against the oracle
+    import json
+    n = (181, nq, 151)
+    pi, pic = (2, 1, 3), (3, 1, 2)
+    J = 37
+    X = synth.integers(n, 4600 + nq)
+    Bm = synth.integers((J, nq), 4601 + nq)
+    A = put(X, pi, cuda_dev, dtype)
+    nout = (181, J, 151)
+    C = torch.empty(int(np.prod(nout)), dtype=TORCH[dtype], device=cuda_dev)
+    rc, js = tl.tl_plan_describe(tl.TL_OP_TTM, tl.Desc(A, n, pi), None, 2, J, 0, 0,
+                                 tl.Desc(C, nout, pic))
+    assert rc == 0 and json.loads(js)["kernel"] == "ttm_rows", js
+    got, ref = ttm_case(tl, cuda_dev, X, 2, Bm, pi, pic, dtype)
+    np.testing.assert_array_equal(got, ref)
+    C0 = synth.integers(nout, 4602)
+    got, ref = ttm_case(tl, cuda_dev, X, 2, Bm, pi, pic, dtype, accumulate=True, C0=C0)
+    np.testing.assert_array_equal(got, ref)
