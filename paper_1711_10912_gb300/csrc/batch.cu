@@ -120,6 +120,14 @@ __device__ __forceinline__ void bdecode(const BOp& op, int64_t g, int64_t& o0, i
     bcheck(op, o0, o1, o2);
 }
 
+// Loads of A per chunk of a strided dot product: 8 FP32 / 4 FP64 keep the
+// persistent kernel within its 64 registers.
+template <typename T>
+constexpr int dot_chunk_len()
+{
+    return sizeof(T) == 4 ? 8 : 4;
+}
+
 template <typename T>
 __device__ void unit_ttv_col(const BOp& op, int64_t e0, int64_t e1)
 {
@@ -128,18 +136,7 @@ __device__ void unit_ttv_col(const BOp& op, int64_t e0, int64_t e1)
     for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
         int64_t oa, oc, unused;
         bdecode(op, e, oa, oc, unused);
-        const T* pa = A + oa;
-        T acc = T(0);
-        int64_t k = 0;
-        for (; k + 4 <= op.nq; k += 4) {
-            T a0 = __ldg(pa + k * op.saq), a1 = __ldg(pa + (k + 1) * op.saq);
-            T a2 = __ldg(pa + (k + 2) * op.saq), a3 = __ldg(pa + (k + 3) * op.saq);
-            acc = fma(a0, __ldg(b + k * op.incb), acc);
-            acc = fma(a1, __ldg(b + (k + 1) * op.incb), acc);
-            acc = fma(a2, __ldg(b + (k + 2) * op.incb), acc);
-            acc = fma(a3, __ldg(b + (k + 3) * op.incb), acc);
-        }
-        for (; k < op.nq; ++k) acc = fma(__ldg(pa + k * op.saq), __ldg(b + k * op.incb), acc);
+        const T acc = dot_strided<T, dot_chunk_len<T>()>(A + oa, op.saq, b, op.incb, op.nq, T(0));
         T* pc = static_cast<T*>(op.C) + oc;
         *pc = op.accumulate ? *pc + acc : acc;
     }
@@ -157,10 +154,34 @@ __device__ __forceinline__ bool ttv_vec_ok(const BOp& op)
     return ((reinterpret_cast<uintptr_t>(op.A) | reinterpret_cast<uintptr_t>(op.C)) & 15) == 0;
 }
 
+// acc[v] += sum over u < NQ of a[u * sa + v] * b[u * sb], u ascending: the
+// chunk's 16-byte loads of A all issued before the first product.
+template <typename T, int NQ>
+__device__ __forceinline__ void vec_chunk(const T* __restrict__ a, int64_t sa, const T* __restrict__ b,
+                                          int64_t sb, T* acc)
+{
+    constexpr int V = 16 / sizeof(T);
+    using VT = typename Vec<T, V>::type;
+    VT x[NQ];
+    T y[NQ];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+        x[u] = __ldg(reinterpret_cast<const VT*>(a + u * sa));
+        y[u] = __ldg(b + u * sb);
+    }
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+        const T* xe = reinterpret_cast<const T*>(&x[u]);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = fma(xe[v], y[u], acc[v]);
+    }
+}
+
 // Outputs contiguous in A and C along the collapsed dim 0 (its extent and
 // every other stride multiples of the vector width, 16-byte aligned bases):
 // each thread takes 16 bytes of consecutive outputs and streams A with
-// 16-byte loads, four k at a time.
+// 16-byte loads, 128 bytes per thread at a time and the remainder as one
+// chunk.
 template <typename T>
 __device__ void unit_ttv_vec(const BOp& op, int64_t e0, int64_t e1)
 {
@@ -175,25 +196,23 @@ __device__ void unit_ttv_vec(const BOp& op, int64_t e0, int64_t e1)
         T acc[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = T(0);
+        // chunks of 128 bytes of A per thread (8 FP32 / 4 FP64 vectors) fit
+        // the kernel's 64 registers
+        constexpr int CH = sizeof(T) == 8 ? 4 : 8;
         int64_t k = 0;
-        for (; k + 4 <= op.nq; k += 4) {
-            VT x[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = __ldg(reinterpret_cast<const VT*>(pa + (k + u) * op.saq));
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const T bk = __ldg(b + (k + u) * op.incb);
-                const T* xe = reinterpret_cast<const T*>(&x[u]);
-#pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] = fma(xe[v], bk, acc[v]);
-            }
-        }
-        for (; k < op.nq; ++k) {
-            const VT x = __ldg(reinterpret_cast<const VT*>(pa + k * op.saq));
-            const T bk = __ldg(b + k * op.incb);
-            const T* xe = reinterpret_cast<const T*>(&x);
-#pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] = fma(xe[v], bk, acc[v]);
+        for (; k + CH <= op.nq; k += CH)
+            vec_chunk<T, CH>(pa + k * op.saq, op.saq, b + k * op.incb, op.incb, acc);
+        const T* at = pa + k * op.saq;
+        const T* bt = b + k * op.incb;
+        switch ((int)(op.nq - k)) {
+        case 1: vec_chunk<T, 1>(at, op.saq, bt, op.incb, acc); break;
+        case 2: vec_chunk<T, 2>(at, op.saq, bt, op.incb, acc); break;
+        case 3: vec_chunk<T, 3>(at, op.saq, bt, op.incb, acc); break;
+        case 4: vec_chunk<T, CH == 8 ? 4 : 1>(at, op.saq, bt, op.incb, acc); break;
+        case 5: vec_chunk<T, CH == 8 ? 5 : 1>(at, op.saq, bt, op.incb, acc); break;
+        case 6: vec_chunk<T, CH == 8 ? 6 : 1>(at, op.saq, bt, op.incb, acc); break;
+        case 7: vec_chunk<T, CH == 8 ? 7 : 1>(at, op.saq, bt, op.incb, acc); break;
+        default: break;
         }
         T* pc = static_cast<T*>(op.C) + oc;
         if (op.accumulate) {
@@ -221,8 +240,11 @@ __device__ void unit_ttv_row(const BOp& op, int64_t e0, int64_t e1)
         int64_t oa = 0, oc = 0, unused;
         if (ok) {
             bdecode(op, e, oa, oc, unused);
-            for (int64_t k = sub; k < op.nq; k += L)
-                acc = fma(__ldg(A + oa + k * op.saq), __ldg(b + k * op.incb), acc);
+            // this lane's k = sub, sub + L, ... in ascending order
+            if (sub < op.nq)
+                acc = dot_strided<T, dot_chunk_len<T>()>(A + oa + sub * op.saq, L * op.saq,
+                                                         b + sub * op.incb, L * op.incb,
+                                                         (op.nq - sub + L - 1) / L, T(0));
         }
 #pragma unroll
         for (int m = L / 2; m >= 1; m /= 2) acc += __shfl_xor_sync(0xffffffffu, acc, m);

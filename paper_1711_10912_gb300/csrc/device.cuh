@@ -345,4 +345,44 @@ __device__ __forceinline__ void row_dot(const T* __restrict__ a, int64_t sa, int
     }
 }
 
+// acc + sum over u < NQ of a[u * sa] * b[u * sb], u ascending, every load of
+// a in the chunk issued before the first product (b, a short vector read by
+// every output, comes from cache).
+template <typename T, int NQ>
+__device__ __forceinline__ T dot_chunk(const T* __restrict__ a, int64_t sa, const T* __restrict__ b,
+                                       int64_t sb, T acc)
+{
+    T x[NQ];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) x[u] = __ldg(a + (int64_t)u * sa);
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) acc = fma(x[u], __ldg(b + (int64_t)u * sb), acc);
+    return acc;
+}
+
+// acc + the strided dot product of length n (Eq. 24 for one output), k
+// ascending: chunks of CH, then the remainder as one chunk of its exact
+// length.
+template <typename T, int CH>
+__device__ __forceinline__ T dot_strided(const T* __restrict__ a, int64_t sa,
+                                         const T* __restrict__ b, int64_t sb, int64_t n, T acc)
+{
+    static_assert(CH == 4 || CH == 8, "chunk of 4 or 8");
+    int64_t k = 0;
+    for (; k + CH <= n; k += CH) acc = dot_chunk<T, CH>(a + k * sa, sa, b + k * sb, sb, acc);
+    const T* at = a + k * sa;
+    const T* bt = b + k * sb;
+    switch ((int)(n - k)) {
+    case 1: acc = dot_chunk<T, 1>(at, sa, bt, sb, acc); break;
+    case 2: acc = dot_chunk<T, 2>(at, sa, bt, sb, acc); break;
+    case 3: acc = dot_chunk<T, 3>(at, sa, bt, sb, acc); break;
+    case 4: acc = dot_chunk<T, CH == 8 ? 4 : 1>(at, sa, bt, sb, acc); break;
+    case 5: acc = dot_chunk<T, CH == 8 ? 5 : 1>(at, sa, bt, sb, acc); break;
+    case 6: acc = dot_chunk<T, CH == 8 ? 6 : 1>(at, sa, bt, sb, acc); break;
+    case 7: acc = dot_chunk<T, CH == 8 ? 7 : 1>(at, sa, bt, sb, acc); break;
+    default: break;
+    }
+    return acc;
+}
+
 }  // namespace tl
