@@ -115,8 +115,11 @@ def test_batch_matches_oracle_default_plan(tl, cuda_dev, dtype):
 @pytest.mark.parametrize("variant,unit", [("TTV_COL", 7), ("TTV_COL", 1000), ("TTV_ROW4", 5),
                                           ("TTV_ROW8", 300), ("TTV_ROW32", 64), ("TTV_VEC", 6),
                                           ("TTV_VEC", 4096)])
-def test_batch_every_ttv_variant(tl, cuda_dev, variant, unit):
-    s = OpSet(tl, cuda_dev, 120, 7100, "f32")
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batch_every_ttv_variant(tl, cuda_dev, variant, unit, dtype):
+    # contractions of 2-24: every remainder of the 8-long (FP32) and 4-long
+    # (FP64) load chunks of the ttv units
+    s = OpSet(tl, cuda_dev, 120, 7100, dtype)
     rc, b = tl.tl_batch_create(s.ops, 0)
     tl.check(rc)
     try:
