@@ -283,3 +283,35 @@ def test_batch_poisoned_tune_cache_is_ignored(tl, cuda_dev, tmp_path):
     assert out and json.loads(out[0])["unfit"] == 0, second.stdout[-2000:]
     assert second.returncode == 0, second.stderr[-2000:]
     assert json.loads(out[-1])["worst"] <= TOL["f32"]
+
+
+def test_batch_keeps_row_unit_ttm_persistent_up_to_256mb(tl, cuda_dev):
+    # a 48 MB ttm whose matrix fits the row unit (n_q = 4, J = 8) runs as
+    # units of the persistent launch; a 20 MB ttv still runs on its own kernel
+    # (16 MB rule); both match the oracle
+    n = (4, 1024, 1024)
+    X = synth.normal(n, 7600, dtype=np.float64)
+    A = put(X, (1, 2, 3), cuda_dev, "f32")
+    Bm = synth.normal((8, 4), 7601, dtype=np.float64)
+    Bt = to_dev(Bm.reshape(-1), cuda_dev, "f32")
+    b = synth.normal((4,), 7602, dtype=np.float64)
+    bt = to_dev(b, cuda_dev, "f32")
+    Cm = torch.empty(8 * 1024 * 1024, dtype=torch.float32, device=cuda_dev)
+    Cv = torch.empty(1024 * 1024, dtype=torch.float32, device=cuda_dev)
+    DA, DCm, DCv = tl.Desc(A, n), tl.Desc(Cm, (8, 1024, 1024)), tl.Desc(Cv, (1024, 1024))
+    opm = tl.make_op(tl.TL_OP_TTM, DA, DCm, q=1, vec=Bt, J=8, ldb_row=4, ldb_col=1)
+    opv = tl.make_op(tl.TL_OP_TTV, DA, DCv, q=1, vec=bt)
+    rc, bh = tl.tl_batch_create([opm, opv], 0)
+    tl.check(rc)
+    try:
+        info = json.loads(tl.tl_batch_describe(bh)[1])
+        assert info["direct"] == 1 and info["ops"] == 1, info
+        tl.check(tl.tl_batch_run(bh))
+        torch.cuda.synchronize()
+        mem = synth.to_memory(X.astype(np.float32), (1, 2, 3))
+        refm = oracle.ttm(mem, n, oracle.strides(n), 1, Bm.reshape(-1).astype(np.float32), 8, 4, 1)
+        refv = oracle.ttv(mem, n, oracle.strides(n), 1, b.astype(np.float32))
+        assert rel_err(Cm.cpu().numpy(), refm) <= 1e-5
+        assert rel_err(Cv.cpu().numpy(), refv) <= 1e-5
+    finally:
+        tl.tl_batch_destroy(bh)
