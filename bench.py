@@ -707,7 +707,8 @@ def main():
         del wl
         torch.cuda.empty_cache()
         if not args.no_batch:
-            extras["batch"] = measure_batch(tl, torch, dev, sh, args.batch_ops)
+            extras["batch"] = measure_batch(tl, torch, dev, sh, args.batch_ops,
+                                            hbm=peaks["hbm_gbs"])
             torch.cuda.empty_cache()
         if not args.no_serve:
             rates = [float(x) for x in args.serve_rates.split(",") if x]
@@ -787,10 +788,11 @@ def _op_for_unit(tl, torch, dev, u, seed, keep):
     return op, call, byts, flops, C
 
 
-def measure_batch(tl, torch, dev, sh, nops, reps=5):
+def measure_batch(tl, torch, dev, sh, nops, reps=5, hbm=None):
     """4096 FP32 ttv/ttm of order 3-6 with random extents and layouts: a plain
     loop of per-call launches against one persistent, graph-captured launch
-    with autotuned units."""
+    with autotuned units; GB/s of algorithmic bytes and, given the measured
+    HBM bandwidth `hbm` (GB/s), its fraction."""
     import synth
     units = synth.batch_units(nops)
     keep, ops, calls, outs = [], [], [], []
@@ -833,6 +835,8 @@ def measure_batch(tl, torch, dev, sh, nops, reps=5):
                      "ops/s": round(nops / (dev_ms / 1e3), 1),
                      "GB/s": round(tot_b / (dev_ms / 1e3) / 1e9, 1),
                      "TFLOP/s": round(tot_f / (dev_ms / 1e3) / 1e12, 3)}
+        if hbm:
+            res[name]["frac_hbm"] = round(tot_b / (dev_ms / 1e3) / 1e9 / hbm, 3)
     # the persistent results equal the per-call results within FP32 tolerance
     ref = [o.clone() for o in outs]
     persistent()
